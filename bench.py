@@ -1,0 +1,331 @@
+#!/usr/bin/env python3
+"""Throughput of batched TaNG packet classification on B300.
+
+Workload: 512k synthetic 5-field rules (prefix lengths {0,8,16,24,32} at {.1,.15,.25,.3,.2},
+ports 50% wildcard / 30% exact / 20% range, protocol 50% wildcard else {6,17,1},
+priority = index) and a 16M-packet trace (8M uniform inside a uniformly chosen rule,
+8M inside a Zipf(1.2)-popular rule, shuffled). The network has the paper's shape (6 residual
+blocks of 512) and is trained on the GPU before timing, outside the timed region.
+
+A step classifies the whole 16M-packet batch (encode + network + exact search + min-priority
+reduction) with inputs resident in HBM (256 MB of headers, larger than the 126 MB L2, so no
+flush is needed between steps). `value` is the fused BF16 kernel's throughput; the FP8 fused
+kernel, the plain FP32 one-kernel-per-stage form and the search without a network are timed on
+the same batch. `e2e` repeats the headline through the C ABI with pinned HOST buffers
+(H2D + D2H inside the timed region).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank runs an independent replica on its own GPU (no collective on the data
+path); the slowest rank's time defines the aggregate.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as wl  # noqa: E402
+
+METRIC = "Mpkt/s at 512k rules, bit-exact rule IDs; p50/p99 latency, fused vs plain"
+N_RULES = 524_288
+N_PACKETS = 16_777_216
+HIDDEN, BLOCKS = 512, 6
+
+
+def flops_per_packet(T):
+    return 2 * 7 * HIDDEN + 2 * BLOCKS * 2 * HIDDEN * HIDDEN + 2 * HIDDEN * T
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d, "measured"
+    except Exception:
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    def __init__(self, index):
+        self.index = index
+        self.samples = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q, "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 8:
+                self.samples.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi samples"]}
+        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for s in self.samples for k in range(4) if s[4 + k].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if os.environ.get("TANG_BENCH_BACKEND", "nccl") == "nccl" else "gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def workload():
+    rules = wl.rules_for_config(2)
+    assert len(rules) == N_RULES
+    trace = wl.trace_for_config(2, rules)
+    assert len(trace) == N_PACKETS
+    return rules, trace
+
+
+def run_reference(args, world, rank):
+    """The oracle (plain C linear scan over rules in priority order) on this host's cores."""
+    if rank != 0:
+        return
+    from oracle import classify as oc
+    rules, trace = workload()
+    cores = os.cpu_count() or 1
+    sample = int(os.environ.get("TANG_REF_SAMPLE", "200000"))
+    h = trace[:sample]
+    for _ in range(max(0, args.warmup)):
+        oc.classify(rules, h[:20000], threads=cores)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oc.classify(rules, h, threads=cores)
+    dt = time.perf_counter() - t0
+    v = args.steps * len(h) / dt / 1e6
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": "Mpkt/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * dt / args.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": "512k rules (synthetic generator), 16M-packet trace; each step a %d-packet sample" % len(h),
+                   "rules": N_RULES, "packets_per_step": len(h)},
+        "cpu_baseline": {"value": round(v, 4), "unit": "Mpkt/s", "cores": cores, "kind": "oracle",
+                         "sample": "first %d packets of the 16M trace per step" % len(h)},
+        "e2e": {"value": round(v, 4), "unit": "Mpkt/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--train-seconds", type=float, default=float(os.environ.get("TANG_TRAIN_SECONDS", "20")))
+    ap.add_argument("--quick", action="store_true", help="skip the secondary measurements")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+
+    import torch
+    torch.cuda.set_device(local)
+    import paper_2601_03187_b300 as tg
+
+    pk, pk_src = peaks()
+    rules, trace = workload()
+    ctx = tg.Context(local)
+    t0 = time.perf_counter()
+    rs = ctx.load_ruleset(rules)
+    info = ctx.ruleset_info(rs)
+    T = info["n_tuples"]
+    load_s = time.perf_counter() - t0
+    # train the network (outside the timed region) on a separate seeded trace
+    train_h = wl.trace_for_config(2, rules, scale=1 / 16, seed=2)
+    blob, rep = ctx.train(rs, train_h, N=HIDDEN, blocks=BLOCKS, batch=8192, epochs=1000, max_rounds=1,
+                          decay_every=200, alpha=1000, beta=0.95, holdout=0.05, time_budget_s=args.train_seconds,
+                          seed=1)
+    ctx.load_model(rs, blob)
+
+    d_h = torch.from_numpy(trace.view(np.uint8).reshape(-1, 16)).cuda()
+    n = N_PACKETS
+    ids = torch.empty(n, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def time_path(path, steps, warmup, graph=True):
+        for _ in range(warmup):
+            ctx.classify(rs, d_h, ids, path=path, graph=graph)
+        torch.cuda.synchronize()
+        barrier(world)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(steps):
+            ctx.classify(rs, d_h, ids, path=path, graph=graph)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        return ev0.elapsed_time(ev1) / 1e3
+
+    # ---- headline: fused BF16, graph-replayed
+    with ClockSampler(local) as clk:
+        dt = time_path("fused_bf16", args.steps, args.warmup)
+    dt = max_over_ranks(dt, world)
+    value = world * n * args.steps / dt / 1e6
+    ids_fused = ids.cpu().numpy().view(np.uint32)
+    st_bf16 = ctx.classify(rs, d_h, ids, path="fused_bf16", stats=True)
+
+    fpp = flops_per_packet(T)
+    ms_launch = dt / args.steps * 1e3
+    achieved_tflops = fpp * n / (ms_launch / 1e3) / 1e12
+    peak = pk.get("bf16_tflops_sustained", 1400.0)
+    extra = {}
+    if not args.quick:
+        dt8 = time_path("fused_fp8", args.steps, args.warmup)
+        extra["fused_fp8_mpkts"] = round(n * args.steps / dt8 / 1e6, 3)
+        st8 = ctx.classify(rs, d_h, ids, path="fused_fp8", stats=True)
+        extra["fp8_nn_accuracy"] = round(st8["nn_correct"] / max(1, st8["matched"]), 5)
+        extra["fp8_ids_equal_bf16"] = bool((ids.cpu().numpy().view(np.uint32) == ids_fused).all())
+        dtp = time_path("plain_fp32", 2, 1)
+        extra["plain_fp32_mpkts"] = round(n * 2 / dtp / 1e6, 3)
+        extra["plain_ids_equal_fused"] = bool((ids.cpu().numpy().view(np.uint32) == ids_fused).all())
+        dtn = time_path("no_nn", args.steps, args.warmup)
+        extra["no_nn_mpkts"] = round(n * args.steps / dtn / 1e6, 3)
+        st_no = ctx.classify(rs, d_h, ids, path="no_nn", stats=True)
+        extra["no_nn_ids_equal_fused"] = bool((ids.cpu().numpy().view(np.uint32) == ids_fused).all())
+        extra["no_nn_probes_per_pkt"] = round(st_no["probes"] / n, 4)
+        extra["no_nn_rule_reads_per_pkt"] = round(st_no["rule_reads"] / n, 4)
+
+        # latency per classify call (device-resident), fused vs plain
+        lat = {}
+        for path, iters in (("fused_bf16", 200), ("plain_fp32", 40)):
+            for bs in (8192, 65536):
+                hb = d_h[:bs]
+                ib = ids[:bs]
+                for _ in range(5):
+                    ctx.classify(rs, hb, ib, path=path, graph=True)
+                torch.cuda.synchronize()
+                ts = []
+                for _ in range(iters):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    ctx.classify(rs, hb, ib, path=path, graph=True)
+                    e1.record(stream)
+                    e1.synchronize()
+                    ts.append(e0.elapsed_time(e1))
+                lat["%s_b%d" % (path, bs)] = {"p50_ms": round(float(np.percentile(ts, 50)), 4),
+                                              "p99_ms": round(float(np.percentile(ts, 99)), 4)}
+        extra["latency"] = lat
+
+    # ---- e2e: host (pinned) buffers through the C ABI, copies inside the timed region
+    ph = torch.empty(n * 16, dtype=torch.uint8, pin_memory=True).numpy()
+    ph[:] = trace.view(np.uint8).reshape(-1)
+    hh = ph.view(wl.HEADER_DTYPE)
+    pout = torch.empty(n, dtype=torch.int32, pin_memory=True).numpy().view(np.uint32)
+    e2e_steps = max(2, args.steps // 2)
+    ctx.classify(rs, hh, pout, path="fused_bf16")
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        ctx.classify(rs, hh, pout, path="fused_bf16")
+    e2e_dt = max_over_ranks(time.perf_counter() - t0, world)
+    e2e = world * n * e2e_steps / e2e_dt / 1e6
+    e2e_equal = bool((pout == ids_fused).all())
+
+    # ---- CPU baseline: the oracle on a bounded sample, all host cores (rank 0 only)
+    cpu = None
+    if rank == 0 and world == 1:
+        from oracle import classify as oc
+        cores = os.cpu_count() or 1
+        sample = int(os.environ.get("TANG_CPU_SAMPLE", "200000"))
+        t0 = time.perf_counter()
+        ref = oc.classify(rules, trace[:sample], threads=cores)
+        cdt = time.perf_counter() - t0
+        cpu = {"value": round(sample / cdt / 1e6, 4), "unit": "Mpkt/s", "cores": cores, "kind": "oracle",
+               "sample": "first %d packets of the 16M trace (linear scan, all cores)" % sample,
+               "ids_match_gpu": bool((ref == ids_fused[:sample]).all())}
+
+    if rank != 0:
+        return
+    clocks = clk.summary()
+    out = {
+        "metric": METRIC, "value": round(value, 3), "unit": "Mpkt/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": "512k rules x 16M-packet trace (config-0 generator; half uniform-inside-rule, half Zipf 1.2)",
+                   "rules": N_RULES, "packets_per_step": n, "tuples": T, "network": "7-512-6x(512,512)-%d" % T,
+                   "path": "fused persistent tcgen05 BF16 kernel, CUDA-graph replay",
+                   "l2": "inputs (256 MB) larger than L2; no flush", "parallelism": "replicas" if world > 1 else "single"},
+        "e2e": {"value": round(e2e, 3), "unit": "Mpkt/s", "h2d_bytes_per_step": n * 16, "d2h_bytes_per_step": n * 4,
+                "ids_equal_device_path": e2e_equal},
+        "gpu_launches": args.steps,
+        "roofline": {"bound": "tensor", "achieved": round(achieved_tflops, 2), "peak": peak, "unit": "TFLOP/s",
+                     "frac": round(achieved_tflops / peak, 4), "traffic": None,
+                     "peak_kind": "bf16 sustained (%s)" % ("of measured" if pk_src == "measured" else "of fallback"),
+                     "flops_per_packet": fpp},
+        "cpu_baseline": cpu,
+        "clocks": clocks,
+        "stats": {"nn_accuracy": round(st_bf16["nn_correct"] / max(1, st_bf16["matched"]), 5),
+                  "probes_per_pkt": round(st_bf16["probes"] / n, 4),
+                  "rule_reads_per_pkt": round(st_bf16["rule_reads"] / n, 4),
+                  "fallback_frac": round(st_bf16["fallback"] / n, 5),
+                  "matched_frac": round(st_bf16["matched"] / n, 5)},
+        "train": {k: (round(v, 4) if isinstance(v, float) else v) for k, v in rep.items()},
+        "ruleset": {"load_s": round(load_s, 3), "tuples": T, "keys": info["n_keys"],
+                    "device_bytes": info["device_bytes"]},
+    }
+    out.update(extra)
+    print(json.dumps(out), flush=True)
+    ctx.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,323 @@
+/*
+ * tang.h -- C ABI of the B300 (sm_103a) TaNG packet classifier.
+ *
+ * TaNG classifies a packet header against a multi-field ruleset in two stages (§4.1.1): a
+ * residual MLP (§5.1) predicts the tuple of the tuple space (§3.3) that holds the answer, then
+ * that tuple's hash table is probed, the candidates are verified field by field, and the
+ * highest-priority matching rule is returned. This library makes the post-verification exact
+ * (the paper's is not: §4.1.1, §7): after a hit in the predicted tuple it also probes every tuple
+ * that holds a better rule overlapping the hit, and after a miss it searches all other tuples in
+ * ascending order of their best priority. The returned rule id is therefore always the one the
+ * definition of §2.1 gives, whatever the network predicts.
+ *
+ * Conventions for every entry point:
+ *   - Return value: TANG_OK (0) or a negative TANG_E* code. No C++ exception crosses the ABI.
+ *     tang_last_error(ctx) describes the last failure on that context (thread-unsafe string).
+ *   - "host" pointers are ordinary CPU memory; "device" pointers are CUDA global memory on the
+ *     context's device. Entry points that accept either say so and take a TANG_MEM_* flag.
+ *   - The caller owns every buffer it passes in; the library copies what it keeps.
+ *   - `stream` is a cudaStream_t passed as void*; NULL means the context's own stream.
+ *     Device-side work is enqueued on that stream; results are valid once it is synchronised
+ *     unless the call says it synchronises itself.
+ *   - A context is single-threaded: do not call into one context from two threads at once
+ *     (the serving engine's own thread is the exception and is internal).
+ */
+#ifndef TANG_H
+#define TANG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------------------------------
+ * Records (§2.1). All fields little-endian, host byte order (no network byte order).
+ * ------------------------------------------------------------------------------------- */
+
+/* One 5-field packet header, 16 bytes. */
+typedef struct tang_header {
+    uint32_t sip, dip; /* source / destination IPv4 address */
+    uint16_t sp, dp;   /* source / destination port */
+    uint8_t proto;     /* IP protocol */
+    uint8_t pad[3];    /* ignored */
+} tang_header;
+
+/* One rule, 32 bytes. SIP/DIP are prefixes of length 0..32 (bits below the length are
+ * ignored); SP/DP are inclusive ranges lo <= p <= hi; the protocol matches exactly unless
+ * proto_wild != 0. A smaller `priority` is a higher priority (Table 1); equal priorities are
+ * ordered by `id`. `id` must be unique within a ruleset and != TANG_NO_MATCH. */
+typedef struct tang_rule {
+    uint32_t sip, dip;
+    uint16_t sp_lo, sp_hi, dp_lo, dp_hi;
+    uint8_t sip_len, dip_len, proto, proto_wild;
+    uint32_t priority, id;
+    uint32_t reserved; /* must be 0 */
+} tang_rule;
+
+#define TANG_NO_MATCH 0xFFFFFFFFu /* id returned when no rule matches */
+
+/* Error codes. */
+#define TANG_OK 0
+#define TANG_EINVAL (-1)       /* bad argument, malformed rule or model blob */
+#define TANG_ENOMEM (-2)       /* device allocation failed or the memory pool refused it */
+#define TANG_ETABLEFULL (-3)   /* a table cannot grow (e.g. more than 2047 tuples) */
+#define TANG_ENOTFOUND (-4)    /* unknown ruleset handle or rule id */
+#define TANG_EDEVICE (-5)      /* a CUDA call failed */
+#define TANG_ETIMEOUT (-6)     /* a bounded wait ran out */
+#define TANG_EUNSUPPORTED (-7) /* valid request this build cannot serve (e.g. shape too large) */
+#define TANG_EEXIST (-8)       /* duplicate rule id */
+#define TANG_EAGAIN (-9)       /* request not finished yet (serving poll) */
+
+/* ---------------------------------------------------------------------------------------
+ * Context
+ * ------------------------------------------------------------------------------------- */
+typedef struct tang_ctx tang_ctx;
+
+/* Create a context on CUDA device `device`. Every device allocation the context makes
+ * (tables, model weights, scratch, serving buffers) is admitted against `pool_bytes`; 0 means
+ * "no cap". Errors: TANG_EINVAL, TANG_EDEVICE. */
+int tang_create(int device, size_t pool_bytes, tang_ctx **out);
+
+/* Synchronise, stop the serving engine, free everything. NULL is ignored. */
+void tang_destroy(tang_ctx *ctx);
+
+/* Text of the last error on this context ("" if none). Owned by the context. */
+const char *tang_last_error(tang_ctx *ctx);
+
+/* Device bytes currently admitted against the pool, and the cap (0 = none). */
+int tang_memory_usage(tang_ctx *ctx, size_t *used, size_t *cap);
+
+/* ---------------------------------------------------------------------------------------
+ * Rulesets: tuple space (§3.3) + exactness certificate
+ * ------------------------------------------------------------------------------------- */
+
+/* Build the tuple space of `n` host rules and upload it. Tuples are the distinct
+ * (sip_len, dip_len) pairs (§3.3: 5-field tuples are built from SIP and DIP), indexed in
+ * order of first appearance over the rules sorted by (priority, id); a (0,0) tuple is
+ * appended if absent so that restricted insertion (§4.2.1) always has a candidate.
+ * Each tuple gets an open-addressing hash table keyed by the header truncated to the
+ * tuple's lengths; the rules under one key form a run sorted by (priority, id).
+ * Per rule, the conflict set (tuples holding a better rule that overlaps it) is computed
+ * on the GPU. n may be 0. Synchronous. On success *rs_out is the ruleset handle.
+ * Errors: TANG_EINVAL (len > 32, lo > hi, id == TANG_NO_MATCH), TANG_EEXIST (duplicate id),
+ * TANG_ETABLEFULL (> 2047 tuples), TANG_ENOMEM. */
+int tang_load_ruleset(tang_ctx *ctx, const tang_rule *rules, uint32_t n, uint32_t *rs_out);
+
+/* Free a ruleset and its model. */
+int tang_unload_ruleset(tang_ctx *ctx, uint32_t rs);
+
+typedef struct tang_ruleset_info {
+    uint32_t n_rules;      /* live rules */
+    uint32_t n_tuples;     /* T: the network's class count C must equal this */
+    uint32_t conflict_words; /* 32-bit words per conflict set: ceil(T/32) */
+    uint32_t n_keys;       /* distinct (tuple, key) runs */
+    uint64_t device_bytes; /* bytes held by the tables (not the model) */
+    double build_ms;       /* host build + upload + conflict kernel */
+} tang_ruleset_info;
+
+int tang_ruleset_info_get(tang_ctx *ctx, uint32_t rs, tang_ruleset_info *out);
+
+/* Tuple t's prefix lengths and best (priority, id), for t < n_tuples; host outputs. */
+int tang_tuple_get(tang_ctx *ctx, uint32_t rs, uint32_t t, uint32_t *sip_len, uint32_t *dip_len,
+                   uint32_t *min_priority, uint32_t *min_id);
+
+/* For a rule id: the tuple it is stored in and its conflict set (conflict_words words,
+ * bit t set if tuple t holds a better rule that overlaps this rule). Host outputs.
+ * Synchronises the context stream. TANG_ENOTFOUND for an unknown id. */
+int tang_rule_conflicts(tang_ctx *ctx, uint32_t rs, uint32_t id, uint32_t *tuple, uint32_t *words);
+
+/* ---------------------------------------------------------------------------------------
+ * Model (§5.1): input FC (S=7 -> N) + k residual blocks (Eq. 1) + output FC (N -> C)
+ * ------------------------------------------------------------------------------------- */
+
+/* Precisions of the network's N x N layers. */
+#define TANG_FP32 0 /* FP32 CUDA-core GEMMs */
+#define TANG_BF16 1 /* tcgen05 BF16 MMA, FP32 accumulation */
+#define TANG_FP8 2  /* tcgen05 FP8 E4M3 MMA, FP32 accumulation, per-channel weight scales */
+
+/* Model blob (little-endian), produced by tang_train() or by the caller:
+ *   tang_model_header
+ *   float act_amax[2*blocks + 1]  -- max |activation| entering each tensor-core layer, in
+ *                                    order h0, u1, h1, u2, h2, ..., uk, hk (used for FP8;
+ *                                    all zero = "not calibrated", FP8 then refused)
+ *   float params[] in this order, each row-major with the x.W convention of Eq. 1
+ *     W0[S][N] b0[N]  { W1[N][N] b1[N] W2[N][N] b2[N] } x blocks  Wc[N][C] bc[C]
+ * W0 acts on the raw 16-bit segment values of §5.2 (SIP hi, SIP lo, DIP hi, DIP lo, SP, DP,
+ * PRO). */
+#define TANG_MODEL_MAGIC 0x474E4154u /* "TANG" */
+typedef struct tang_model_header {
+    uint32_t magic;   /* TANG_MODEL_MAGIC */
+    uint32_t version; /* 1 */
+    uint32_t S, N, blocks, C;
+    uint32_t reserved[10];
+} tang_model_header; /* 64 bytes */
+
+/* Validate and upload a model for ruleset `rs`; keeps an FP32 copy and derives the BF16 and
+ * (if calibrated) FP8 copies. Requires C == n_tuples, S == 7. The tensor-core paths further
+ * require N == 512 (other N use the FP32 path only) and C <= 256.
+ * Replaces a previous model of the ruleset. Synchronous.
+ * Errors: TANG_EINVAL (bad magic, sizes, C != T), TANG_ENOMEM. */
+int tang_load_model(tang_ctx *ctx, uint32_t rs, const void *blob, size_t bytes);
+
+/* ---------------------------------------------------------------------------------------
+ * Classification (§4.1.1)
+ * ------------------------------------------------------------------------------------- */
+
+/* Path selection (flags & TANG_PATH_MASK). */
+#define TANG_PATH_FUSED_BF16 0x0 /* one persistent kernel: encode + BF16 MLP + search */
+#define TANG_PATH_FUSED_FP8 0x1  /* same with FP8 layers */
+#define TANG_PATH_PLAIN_FP32 0x2 /* one kernel per stage, FP32 CUDA-core MLP */
+#define TANG_PATH_STAGED_BF16 0x3 /* BF16 MLP kernel, then a separate search kernel */
+#define TANG_PATH_NO_NN 0x4      /* no network: every tuple in ascending best priority */
+#define TANG_PATH_STAGED_FP8 0x5
+#define TANG_PATH_MASK 0xF
+/* Where `headers` / `ids` live. */
+#define TANG_MEM_DEVICE 0x00      /* both device pointers */
+#define TANG_MEM_HOST 0x10        /* both host pointers (pageable or pinned); the call pipelines
+                                     H2D, compute and D2H on side streams and returns when `ids`
+                                     is filled (synchronous) */
+/* Other flags. */
+#define TANG_GRAPH 0x100          /* DEVICE mode: capture the launch sequence in a CUDA graph
+                                     keyed by (ruleset, path, n, pointers, stream) and replay it */
+
+typedef struct tang_stats {
+    uint64_t packets;       /* packets classified */
+    uint64_t matched;       /* packets with a matching rule */
+    uint64_t nn_correct;    /* matched packets whose predicted tuple holds the answer */
+    uint64_t pred_hit;      /* predicted tuple had a matching rule */
+    uint64_t fallback;      /* predicted tuple had no match: ordered search of the rest */
+    uint64_t probes;        /* tuple hash-table probes (predicted tuple counts as one) */
+    uint64_t rule_reads;    /* rule records compared */
+    uint64_t slot_reads;    /* hash slots read */
+} tang_stats;
+
+/* Classify n headers into rule ids (ids[i] = matching rule's id or TANG_NO_MATCH).
+ * The rule id never depends on the path or precision (exact post-verification).
+ * DEVICE mode: asynchronous on `stream`. HOST mode: synchronous.
+ * `stats` (may be NULL) receives counters for this call; passing it synchronises.
+ * n == 0 is allowed. Errors: TANG_ENOTFOUND (rs), TANG_EINVAL (path needs a model that
+ * is not loaded, bad flags, unaligned pointer), TANG_EUNSUPPORTED, TANG_EDEVICE. */
+int tang_classify(tang_ctx *ctx, uint32_t rs, const tang_header *headers, uint32_t n, uint32_t *ids,
+                  uint32_t flags, void *stream, tang_stats *stats);
+
+/* Stage 1 alone (§4.1.1): run the network of ruleset rs over n device headers.
+ * d_logits (device, n x C float, row-major; may be NULL) receives the output layer's logits;
+ * d_tuple (device, n int32; may be NULL) the argmax (lowest index on ties).
+ * precision: TANG_FP32 / TANG_BF16 / TANG_FP8. Asynchronous on `stream`. */
+int tang_infer(tang_ctx *ctx, uint32_t rs, const tang_header *d_headers, uint32_t n, float *d_logits,
+               int32_t *d_tuple, int precision, void *stream);
+
+/* Stage 2 alone: exact search of n device headers given predicted tuples d_tuple (device,
+ * n int32; NULL = no prediction, i.e. the ordered search over all tuples). Values outside
+ * [0, T) are treated as "no prediction". Writes d_ids (device). `stats` as in classify. */
+int tang_search(tang_ctx *ctx, uint32_t rs, const tang_header *d_headers, const int32_t *d_tuple, uint32_t n,
+                uint32_t *d_ids, void *stream, tang_stats *stats);
+
+/* ---------------------------------------------------------------------------------------
+ * Immediate update (§4.2.1). Stream-ordered: every classify issued after the call (on any
+ * stream) sees it. Neither call creates or removes a tuple, so a loaded model stays valid.
+ * ------------------------------------------------------------------------------------- */
+
+/* Insert into the tuple with the rule's exact lengths, else into the first tuple of largest
+ * length sum among those with lengths <= the rule's (the rule is truncated into it; its own
+ * lengths are still verified). Updates the conflict sets of the affected rules on the GPU.
+ * Errors: TANG_EINVAL, TANG_EEXIST (id already live), TANG_ENOMEM. */
+int tang_insert_rule(tang_ctx *ctx, uint32_t rs, const tang_rule *rule);
+
+/* Remove a live rule. Conflict sets of other rules are left as supersets (still exact).
+ * Errors: TANG_ENOTFOUND. */
+int tang_delete_rule(tang_ctx *ctx, uint32_t rs, uint32_t id);
+
+/* Rules inserted since load whose lengths differ from their tuple's (the deferred-update
+ * counter of §4.2.2). */
+int tang_suboptimal_count(tang_ctx *ctx, uint32_t rs, uint64_t *count);
+
+/* ---------------------------------------------------------------------------------------
+ * Training (§5.2), all on the GPU with this library's own forward/backward kernels
+ * ------------------------------------------------------------------------------------- */
+
+typedef struct tang_train_cfg {
+    uint32_t N;             /* neurons per FC layer (paper: 512) */
+    uint32_t blocks;        /* residual blocks (paper: 6) */
+    uint32_t batch;         /* minibatch (paper: 8192) */
+    uint32_t epochs;        /* epochs per round (paper: 1000) */
+    uint32_t max_rounds;    /* rounds of the alpha schedule */
+    uint32_t decay_every;   /* epochs between lr decays (paper: 200) */
+    float lr;               /* initial Adam learning rate (paper: 1e-3) */
+    float decay;            /* lr factor per decay (paper: 0.1) */
+    uint32_t alpha;         /* class-balance threshold (paper: 1000), x10 per failed round */
+    float beta;             /* accuracy threshold (paper: 0.95) */
+    float holdout;          /* fraction of labelled samples held out for the accuracy check */
+    float time_budget_s;    /* stop training after this many seconds (0 = no limit) */
+    uint64_t seed;          /* initialisation, shuffling, oversampling */
+} tang_train_cfg;
+
+typedef struct tang_train_report {
+    uint32_t rounds, epochs_run, samples_labelled, samples_trained, classes_empty;
+    uint32_t alpha_final;
+    float final_loss, holdout_accuracy, train_seconds;
+} tang_train_report;
+
+/* Label n host sample headers with the tuple of their exact match (unmatched samples are
+ * dropped), oversample every class below alpha, and train the network of §5.1 on it with
+ * cross-entropy and Adam; repeat rounds with alpha x10 while holdout accuracy < beta (§5.2).
+ * On success writes a model blob (calibrated FP8 amax included) to `blob` if *bytes is large
+ * enough, and always sets *bytes to the blob size (call with blob == NULL to size it).
+ * report may be NULL. Synchronous. */
+int tang_train(tang_ctx *ctx, uint32_t rs, const tang_header *samples, uint32_t n, const tang_train_cfg *cfg,
+               void *blob, size_t *bytes, tang_train_report *report);
+
+/* Forward + backward of the mean cross-entropy for one batch, on the GPU (the trainer's
+ * kernels), for gradient checks. params/grads are host float arrays in the blob's parameter
+ * order (sizes from S, N, blocks, C); headers/labels are host arrays of n entries; features
+ * are the raw segments times `input_scale`. Writes *loss and grads. Synchronous. */
+int tang_loss_grad(tang_ctx *ctx, uint32_t S, uint32_t N, uint32_t blocks, uint32_t C, const float *params,
+                   const tang_header *headers, const int32_t *labels, uint32_t n, float input_scale,
+                   float *loss, float *grads);
+
+/* One Adam step (bias-corrected, step number t >= 1) over `count` host floats on the GPU. */
+int tang_adam_step(tang_ctx *ctx, float *params, const float *grads, float *m, float *v, uint64_t count,
+                   uint32_t t, float lr, float beta1, float beta2, float eps);
+
+/* ---------------------------------------------------------------------------------------
+ * Autotuning and serving
+ * ------------------------------------------------------------------------------------- */
+
+/* Time the fused kernel's launch variants (CTAs per SM, pipeline stages, search mode) on
+ * `n` device headers and keep the fastest per (ruleset, path). Synchronous. */
+int tang_autotune(tang_ctx *ctx, uint32_t rs, const tang_header *d_headers, uint32_t n, uint32_t flags);
+
+typedef struct tang_serve_cfg {
+    uint32_t max_inflight;   /* requests on the GPU at once (slots) */
+    uint32_t max_batch;      /* packets per GPU launch (requests are packed up to this) */
+    uint32_t path;           /* TANG_PATH_* used for every launch */
+    uint32_t reserved;
+} tang_serve_cfg;
+
+typedef struct tang_req_stats {
+    double submit_s, start_s, done_s; /* seconds on the context's monotonic clock */
+} tang_req_stats;
+
+/* Start the continuous-batching engine: a host thread packs queued requests (of any
+ * rulesets) into GPU launches as slots and pool memory free up, overlaps their work on
+ * several streams, and completes requests out of order. */
+int tang_serve_start(tang_ctx *ctx, const tang_serve_cfg *cfg);
+/* Queue a request of n host headers against ruleset rs; ids (host, n entries) is written
+ * before the request completes. Both buffers must stay valid until then. */
+int tang_serve_submit(tang_ctx *ctx, uint32_t rs, const tang_header *headers, uint32_t n, uint32_t *ids,
+                      uint64_t *req_id);
+/* TANG_OK when done (stats filled, may be NULL), TANG_EAGAIN while pending after waiting up
+ * to wait_ms, TANG_ENOTFOUND for an unknown id. A completed id is forgotten after poll. */
+int tang_serve_poll(tang_ctx *ctx, uint64_t req_id, int wait_ms, tang_req_stats *stats);
+/* Drain and stop. */
+int tang_serve_stop(tang_ctx *ctx);
+/* Seconds on the clock used by tang_req_stats. */
+double tang_now(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TANG_H */

@@ -1,0 +1,122 @@
+// Device functions of the exact tuple-space search (stage 2 of §4.1.1), shared by the staged
+// search kernel (search.cu) and the fused classification kernel (mlp_tc.cu).
+#pragma once
+
+#include "internal.h"
+
+namespace tang {
+
+// MurmurHash3 fmix64 finalizer (Austin Appleby, public domain); same as fmix64_host().
+__device__ __forceinline__ uint64_t fmix64(uint64_t k) {
+    k ^= k >> 33;
+    k *= 0xff51afd7ed558ccdULL;
+    k ^= k >> 33;
+    k *= 0xc4ceb9fe1a85ec53ULL;
+    k ^= k >> 33;
+    return k;
+}
+
+struct Hdr {
+    uint32_t sip, dip, sp, dp, proto;
+};
+
+__device__ __forceinline__ Hdr load_header(const tang_header *h) {
+    uint4 v = __ldg(reinterpret_cast<const uint4 *>(h));
+    return Hdr{v.x, v.y, v.z & 0xFFFFu, v.z >> 16, v.w & 0xFFu};
+}
+
+__device__ __forceinline__ DRule load_rule(const DRule *r) {
+    uint4 a = __ldg(reinterpret_cast<const uint4 *>(r));
+    uint4 b = __ldg(reinterpret_cast<const uint4 *>(r) + 1);
+    return DRule{a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+}
+
+// Rule conditions of §2.1 on the rule's own prefix lengths (also for rules truncated into a
+// coarser tuple by restricted insertion).
+__device__ __forceinline__ bool rule_match(const DRule &r, const Hdr &h) {
+    uint32_t m = r.meta;
+    bool ok = ((h.sip ^ r.sip) & prefix_mask(meta_sip_len(m))) == 0;
+    ok &= ((h.dip ^ r.dip) & prefix_mask(meta_dip_len(m))) == 0;
+    ok &= (h.sp >= (r.sp & 0xFFFFu)) & (h.sp <= (r.sp >> 16));
+    ok &= (h.dp >= (r.dp & 0xFFFFu)) & (h.dp <= (r.dp >> 16));
+    ok &= (!meta_proto_exact(m)) | (h.proto == meta_proto(m));
+    return ok;
+}
+
+// The best match found so far, ordered by (priority, id).
+struct Best {
+    uint32_t prio, id, pos, cf, tuple;
+};
+
+__device__ __forceinline__ bool beats(uint32_t prio, uint32_t id, const Best &b) {
+    return prio < b.prio || (prio == b.prio && id < b.id);
+}
+
+struct Counters {
+    uint32_t probes, rule_reads, slot_reads;
+};
+
+// Probe tuple t with the header truncated to the tuple's lengths (§3.3); scan the run under
+// that key in (priority, id) order and stop at the first match or at the first rule that does
+// not beat the current best. Returns true if `best` improved.
+__device__ __forceinline__ bool probe_tuple(const Tables &tb, const TupleDesc &d, uint32_t t, const Hdr &h,
+                                            Best &best, Counters &c) {
+    const uint32_t ks = h.sip & d.mask_s, kd = h.dip & d.mask_d;
+    const uint32_t start = uint32_t(fmix64((uint64_t(ks) << 32) | kd)) & d.slot_mask;
+    for (uint32_t i = 0; i <= d.max_probe; ++i) {
+        uint4 s = __ldg(reinterpret_cast<const uint4 *>(tb.slots + d.slot_base + ((start + i) & d.slot_mask)));
+        c.slot_reads++;
+        if (s.z == kEmpty) return false;
+        if (s.x == ks && s.y == kd) {
+            for (uint32_t j = 0; j < s.w; ++j) {
+                DRule r = load_rule(tb.rules + s.z + j);
+                c.rule_reads++;
+                if (!beats(r.prio, r.id, best)) return false;
+                if (rule_match(r, h)) {
+                    best = Best{r.prio, r.id, s.z + j, r.cf, t};
+                    return true;
+                }
+            }
+            return false;
+        }
+    }
+    return false;
+}
+
+// Full exact search of one header. `tuples` / `order` may point to shared-memory copies.
+// pred outside [0, T) means "no prediction". Returns true if the predicted tuple held a match.
+__device__ __forceinline__ bool search_packet(const Tables &tb, const TupleDesc *tuples, const uint16_t *order,
+                                              const Hdr &h, int pred, Best &best, Counters &c) {
+    const uint32_t T = tb.T;
+    best = Best{0xFFFFFFFFu, 0xFFFFFFFFu, kEmpty, 0u, 0u};
+    bool hit = false;
+    if (uint32_t(pred) < T) {
+        c.probes++;
+        hit = probe_tuple(tb, tuples[pred], uint32_t(pred), h, best, c);
+    }
+    // After a hit r: only tuples in conflict(r) can hold a better match. After a miss: all.
+    uint32_t cf0 = 0xFFFFFFFFu;
+    const uint32_t *cfw = nullptr;
+    if (hit) {
+        if (tb.cw == 1)
+            cf0 = best.cf;
+        else
+            cfw = tb.cwords + size_t(best.cf) * tb.cw;
+    }
+    for (uint32_t k = 0; k < T; ++k) {
+        const uint32_t t = order[k];
+        if (int(t) == pred) continue;
+        if (hit) {
+            uint32_t w = cfw ? __ldg(cfw + (t >> 5)) : cf0;
+            if (!((w >> (t & 31)) & 1u)) continue;
+        }
+        const TupleDesc d = tuples[t];
+        // tuples come in ascending best (priority, id): none from here on can win
+        if (!beats(d.min_prio, d.min_id, best)) break;
+        c.probes++;
+        probe_tuple(tb, d, t, h, best, c);
+    }
+    return hit;
+}
+
+}  // namespace tang

@@ -1,0 +1,126 @@
+"""Tensor-core (tcgen05) paths: BF16 / FP8 logits against the float64 oracle forward of the same
+quantised weights, and bit-exact rule ids through the fused and staged kernels."""
+import numpy as np
+import pytest
+import torch
+
+import paper_2601_03187_b300 as tg
+import workloads as wl
+from gpu_util import ids_dev, ids_host, logit_tolerance, random_params, to_dev
+from oracle import classify as oc
+from oracle import mlp, quant
+
+pytestmark = pytest.mark.gpu
+
+U32 = 2.0 ** -24
+U_BF16 = 2.0 ** -8   # BF16 keeps 8 significant bits
+U_E4M3 = 2.0 ** -4   # E4M3 keeps 4
+
+
+@pytest.fixture(scope="module")
+def setup():
+    ctx = tg.Context(0)
+    rules = wl.rules_for_config(0)
+    rs = ctx.load_ruleset(rules)
+    T = ctx.ruleset_info(rs)["n_tuples"]
+    p = random_params(np.random.default_rng(77), N=512, blocks=6, C=T)
+    h = wl.trace_for_config(0, rules, seed=5)
+    X = mlp.features(h[:4096])
+    p64 = {k: ([a.astype(np.float64) for a in v] if isinstance(v, list) else v.astype(np.float64)) for k, v in p.items()}
+    # activation calibration (max |input| of every tensor-core layer) on the oracle side
+    _, cache = mlp.forward(p64, X, keep=True)
+    amax = []
+    for k in range(6):
+        amax += [np.abs(cache["h_in"][k]).max(), np.abs(cache["u"][k]).max()]
+    amax.append(np.abs(cache["h_out"]).max())
+    ctx.load_model(rs, tg.pack_model(p, np.array(amax, dtype=np.float32)))
+    yield ctx, rules, rs, T, p, p64, h
+    ctx.close()
+
+
+def bf16_weights(p64):
+    q = dict(p64)
+    for k in ("W1", "W2"):
+        q[k] = [quant.bf16_round(w.astype(np.float32)).astype(np.float64) for w in p64[k]]
+    q["Wc"] = quant.bf16_round(p64["Wc"].astype(np.float32)).astype(np.float64)
+    return q
+
+
+def e4m3_weights(p64):
+    """Per-output-channel scale 448 / max|W[:, n]|, E4M3 round-to-nearest-even, dequantised."""
+    def deq(W):
+        amax = np.abs(W.astype(np.float32)).max(axis=0)
+        sw = np.where(amax > 0, np.float32(448.0) / amax.astype(np.float32), np.float32(1.0)).astype(np.float32)
+        q = quant.e4m3_round((W.astype(np.float32) * sw[None, :]).astype(np.float32))
+        return q / sw[None, :].astype(np.float64)
+    q = dict(p64)
+    q["W1"] = [deq(w) for w in p64["W1"]]
+    q["W2"] = [deq(w) for w in p64["W2"]]
+    q["Wc"] = deq(p64["Wc"])
+    return q
+
+
+def infer(ctx, rs, h, C, precision):
+    d = to_dev(h)
+    z = torch.zeros((len(h), C), dtype=torch.float32, device="cuda")
+    t = torch.zeros(len(h), dtype=torch.int32, device="cuda")
+    ctx.infer(rs, d, z, t, precision=precision)
+    torch.cuda.synchronize()
+    return z.cpu().numpy().astype(np.float64), t.cpu().numpy()
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp8"])
+def test_logits_within_bound(setup, prec):
+    ctx, rules, rs, T, p, p64, h = setup
+    hs = h[:4096]
+    X = mlp.features(hs)
+    q = bf16_weights(p64) if prec == "bf16" else e4m3_weights(p64)
+    z64 = mlp.forward(q, X)
+    z, tup = infer(ctx, rs, hs, T, tg.BF16 if prec == "bf16" else tg.FP8)
+    tol = logit_tolerance(q, X, U32, U_BF16 if prec == "bf16" else U_E4M3)
+    err = np.abs(z - z64)
+    assert np.isfinite(z).all()
+    assert (err <= tol).all(), float((err / tol).max())
+    assert (tup == np.argmax(z, axis=1)).all()
+    # the bound is loose; the typical error is far below it
+    rel = err / (np.abs(z64).max(axis=1, keepdims=True) + 1e-30)
+    assert np.median(rel) < (0.02 if prec == "bf16" else 0.3)
+
+
+@pytest.mark.parametrize("path", ["fused_bf16", "staged_bf16", "fused_fp8", "staged_fp8"])
+def test_ids_exact(setup, path):
+    ctx, rules, rs, T, p, p64, h = setup
+    want = oc.classify(rules, h)
+    d = to_dev(h)
+    ids = ids_dev(len(h))
+    st = ctx.classify(rs, d, ids, path=path, stats=True)
+    assert (ids_host(ids) == want).all()
+    assert st["packets"] == len(h)
+    assert st["pred_hit"] + st["fallback"] == len(h)
+
+
+def test_ragged_sizes_and_graph(setup):
+    ctx, rules, rs, T, p, p64, h = setup
+    for n in (1, 5, 127, 128, 129, 1000, 148 * 128 + 3):
+        hs = h[:n]
+        d = to_dev(hs)
+        ids = ids_dev(n)
+        ctx.classify(rs, d, ids, path="fused_bf16")
+        torch.cuda.synchronize()
+        assert (ids_host(ids) == oc.classify(rules, hs)).all(), n
+    d = to_dev(h)
+    want = oc.classify(rules, h)
+    for _ in range(3):
+        ids = ids_dev(len(h))
+        ctx.classify(rs, d, ids, path="fused_bf16", graph=True)
+        torch.cuda.synchronize()
+        assert (ids_host(ids) == want).all()
+
+
+def test_predictions_agree_across_precisions(setup):
+    """BF16 and FP32 argmax agree on most packets; disagreements are counted, ids stay exact."""
+    ctx, rules, rs, T, p, p64, h = setup
+    hs = h[:20000]
+    _, t32 = infer(ctx, rs, hs, T, tg.FP32)
+    _, t16 = infer(ctx, rs, hs, T, tg.BF16)
+    assert (t32 == t16).mean() > 0.9
