@@ -115,7 +115,19 @@ def load_library(path: str = LIB_PATH):
     return lib
 
 
-lib = load_library()
+class _Lib:
+    """The loaded library, opened on first use (so the build step can import this package before
+    libtang.so exists); a missing library raises at that first use."""
+
+    _real = None
+
+    def __getattr__(self, name):
+        if _Lib._real is None:
+            _Lib._real = load_library()
+        return getattr(_Lib._real, name)
+
+
+lib = _Lib()
 
 # Extra entry points that a build may add beside the ones above.
 EXPORTED = sorted(_SIGS)
