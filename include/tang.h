@@ -215,6 +215,28 @@ int tang_infer(tang_ctx *ctx, uint32_t rs, const tang_header *d_headers, uint32_
 int tang_search(tang_ctx *ctx, uint32_t rs, const tang_header *d_headers, const int32_t *d_tuple, uint32_t n,
                 uint32_t *d_ids, void *stream, tang_stats *stats);
 
+/* Staged BF16 classification (the tensor-core network kernel, then the search kernel) for
+ * callers that must not allocate device memory during a call: code running inside a custom
+ * allocator or allocation hook, processes whose device memory is fixed at start-up, and
+ * latency-bound loops that cannot take the device synchronisation cudaMalloc implies.
+ * tang_classify may grow the context's scratch buffer with cudaMalloc; this entry point instead
+ * passes the predicted tuples between the two kernels through a static device array of
+ * TANG_NOALLOC_MAX_PACKETS int32 entries (4 MiB) that every GPU loading the library holds until
+ * the process exits. It calls no cudaMalloc, cudaFree or allocating library routine.
+ * The paper has no counterpart; it is an addition of this library.
+ *   d_headers: n device headers, 16-byte aligned; d_ids: n device outputs (same ids as
+ *   tang_classify). Requires a loaded model with a tensor-core copy (N == 512, 6 blocks).
+ *   The first call on a device looks up the array's device address (cudaGetSymbolAddress),
+ *   so make that first call before any stream capture that should contain later calls.
+ *   All calls share the one array: calls whose kernels overlap on the GPU (on different
+ *   streams, or from different contexts on the same device) race and must be serialised.
+ *   Asynchronous on `stream` (NULL = the context's stream).
+ * Errors: TANG_EINVAL (n > TANG_NOALLOC_MAX_PACKETS, unaligned or null buffers, no model),
+ * TANG_ENOTFOUND, TANG_EDEVICE. */
+#define TANG_NOALLOC_MAX_PACKETS 1048576u
+int tang_classify_noalloc(tang_ctx *ctx, uint32_t rs, const tang_header *d_headers, uint32_t n, uint32_t *d_ids,
+                          void *stream);
+
 /* ---------------------------------------------------------------------------------------
  * Immediate update (§4.2.1). Stream-ordered: every classify issued after the call (on any
  * stream) sees it. Neither call creates or removes a tuple, so a loaded model stays valid.

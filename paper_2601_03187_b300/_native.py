@@ -101,6 +101,7 @@ _SIGS = {
     "tang_serve_poll": (_I, [_P, _U64, _I, ctypes.POINTER(ReqStats)]),
     "tang_serve_stop": (_I, [_P]),
     "tang_now": (ctypes.c_double, []),
+    "tang_classify_noalloc": (_I, [_P, _U32, _P, _U32, _P, _P]),
 }
 
 
@@ -310,6 +311,12 @@ class Context:
         self._ck(lib.tang_search(self._h, rs, _ptr(headers), _ptr(tuples), n, _ptr(ids), _stream(stream),
                                  ctypes.byref(st) if stats else None), "search")
         return st.as_dict() if stats else None
+
+    def classify_noalloc(self, rs: int, headers, ids, stream=None):
+        """Staged BF16 classify whose inter-kernel scratch is a static device array (no allocation)."""
+        n = _n_headers(headers)
+        self._ck(lib.tang_classify_noalloc(self._h, rs, _ptr(headers), n, _ptr(ids), _stream(stream)),
+                 "classify_noalloc")
 
     # -- updates ----------------------------------------------------------------------------
     def insert_rule(self, rs: int, rule):
