@@ -134,6 +134,114 @@ def workload():
     return rules, trace
 
 
+def quick_model(ctx, rs, rules, seed):
+    """A calibrated network from one short training epoch (serving / update measurements)."""
+    h = wl.gen_trace(rules, [("inside", 16384)], seed)
+    blob, _ = ctx.train(rs, h, N=HIDDEN, blocks=BLOCKS, batch=8192, epochs=1, max_rounds=1, alpha=10, holdout=0.05,
+                        seed=seed)
+    ctx.load_model(rs, blob)
+
+
+def measure_serving(tg, ctx, seconds=2.0):
+    """Four resident rulesets (16k, 64k, 256k, 512k), Poisson arrivals, batch sizes log-uniform in
+    [1, 65536], offered at 0.5 / 0.8 / 0.95 of the measured fused-kernel capacity."""
+    import torch
+    sizes = [16_384, 65_536, 262_144, 524_288]
+    sets, pools = [], []
+    for k, n in enumerate(sizes):
+        rules = wl.gen_rules(n, 10 + k)
+        rs = ctx.load_ruleset(rules)
+        quick_model(ctx, rs, rules, 20 + k)
+        sets.append(rs)
+        pools.append(wl.gen_trace(rules, [("inside", 1 << 20), ("zipf", 1 << 20, 1.2)], 30 + k))
+    # capacity: fused BF16 throughput on 1M-packet batches, averaged over the rulesets
+    caps = []
+    for rs, pool in zip(sets, pools):
+        d = torch.from_numpy(pool[: 1 << 20].view(np.uint8).reshape(-1, 16)).cuda()
+        ids = torch.empty(1 << 20, dtype=torch.int32, device="cuda")
+        ctx.classify(rs, d, ids, path="fused_bf16")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(3):
+            ctx.classify(rs, d, ids, path="fused_bf16")
+        torch.cuda.synchronize()
+        caps.append(3 * (1 << 20) / (time.perf_counter() - t0) / 1e6)
+    capacity = float(np.mean(caps))
+    mean_batch = 65536 / np.log(65537)
+    ctx.serve_start(max_inflight=4, max_batch=262_144, path="fused_bf16")
+    loads = []
+    for rho in (0.5, 0.8, 0.95):
+        rate = rho * capacity * 1e6 / mean_batch
+        arr = wl.gen_serving_arrivals(int(rate * seconds) + 1, len(sets), rate, seed=int(rho * 100))
+        outs, handles, subs = [], [], []
+        t_start = time.perf_counter()
+        for (t_arr, which, size, seed) in arr:
+            delay = t_start + t_arr - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            pool = pools[which]
+            off = seed % (len(pool) - size)
+            h = pool[off: off + size]
+            out = np.empty(size, dtype=np.uint32)
+            outs.append(out)
+            handles.append(ctx.serve_submit(sets[which], h, out))
+        stats = [ctx.serve_poll(r, wait_ms=60000) for r in handles]
+        lat = [1e3 * (s["done_s"] - s["submit_s"]) for s in stats]
+        pk = sum(a[2] for a in arr)
+        span = max(s["done_s"] for s in stats) - min(s["submit_s"] for s in stats)
+        loads.append({"rho": rho, "offered_mpkts": round(rho * capacity, 2), "achieved_mpkts": round(pk / span / 1e6, 2),
+                      "requests": len(arr), "p50_ms": round(float(np.percentile(lat, 50)), 3),
+                      "p99_ms": round(float(np.percentile(lat, 99)), 3)})
+    ctx.serve_stop()
+    for rs in sets:
+        ctx.unload_ruleset(rs)
+    return {"rulesets": sizes, "capacity_mpkts": round(capacity, 2), "batch": "log-uniform [1, 65536]",
+            "slots": 4, "max_batch": 262_144, "loads": loads}
+
+
+def measure_updates(tg, ctx, n_ops=300):
+    """1M rules under an operation stream: 10% inserts/deletes, 90% lookup batches of 4k-256k
+    packets (rounded up to 4k/16k/64k/256k), graph-replayed device classify that sees every
+    preceding update; throughput counts lookup packets over the wall time of the whole stream."""
+    import torch
+    rules = wl.rules_for_config(4)
+    t0 = time.perf_counter()
+    rs = ctx.load_ruleset(rules)
+    load_s = time.perf_counter() - t0
+    quick_model(ctx, rs, rules, 44)
+    ops = wl.gen_update_stream(rules, n_ops, seed=3)
+    pool = wl.gen_trace(rules, [("inside", 1 << 20), ("zipf", 1 << 20, 1.2)], 45)
+    d = torch.from_numpy(pool.view(np.uint8).reshape(-1, 16)).cuda()
+    ids = torch.empty(len(pool), dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+    pk = ins = dels = 0
+    t_upd = 0.0
+    t0 = time.perf_counter()
+    for op in ops:
+        if op[0] == "insert":
+            u0 = time.perf_counter()
+            ctx.insert_rule(rs, op[1])
+            t_upd += time.perf_counter() - u0
+            ins += 1
+        elif op[0] == "delete":
+            u0 = time.perf_counter()
+            ctx.delete_rule(rs, op[1])
+            t_upd += time.perf_counter() - u0
+            dels += 1
+        else:
+            # lookup sizes are rounded up to four buckets so that the captured graphs are replayed
+            n = next(b for b in (4096, 16384, 65536, 262144) if b >= op[1])
+            ctx.classify(rs, d[:n], ids[:n], path="fused_bf16", graph=True)
+            pk += n
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    out = {"rules": len(rules), "ops": n_ops, "inserts": ins, "deletes": dels, "lookup_packets": pk,
+           "mpkts_under_updates": round(pk / dt / 1e6, 2), "update_call_ms_mean": round(1e3 * t_upd / max(1, ins + dels), 3),
+           "ruleset_load_s": round(load_s, 2), "suboptimal_inserts": ctx.suboptimal_count(rs)}
+    ctx.unload_ruleset(rs)
+    return out
+
+
 def run_reference(args, world, rank):
     """The oracle (plain C linear scan over rules in priority order) on this host's cores."""
     if rank != 0:
@@ -268,6 +376,8 @@ def main():
                 lat["%s_b%d" % (path, bs)] = {"p50_ms": round(float(np.percentile(ts, 50)), 4),
                                               "p99_ms": round(float(np.percentile(ts, 99)), 4)}
         extra["latency"] = lat
+        extra["serving"] = measure_serving(tg, ctx)
+        extra["updates"] = measure_updates(tg, ctx)
 
     # ---- e2e: host (pinned) buffers through the C ABI, copies inside the timed region
     ph = torch.empty(n * 16, dtype=torch.uint8, pin_memory=True).numpy()

@@ -369,7 +369,7 @@ static int enqueue_classify(tang_ctx *ctx, Ruleset &rs, const tang_header *h, ui
     switch (path) {
         case TANG_PATH_NO_NN: {
             cudaError_t e = launch_search(rs.d_desc, uint32_t(rs.host.tuples.size()), cw, h, nullptr, n, ids, stats,
-                                          tune ? tune->search_mode : 0, st);
+                                          tune, st);
             if (e != cudaSuccess) return set_err(ctx, TANG_EDEVICE, "search: %s", cudaGetErrorString(e));
             return TANG_OK;
         }
@@ -393,7 +393,7 @@ static int enqueue_classify(tang_ctx *ctx, Ruleset &rs, const tang_header *h, ui
                 rc = run_infer(ctx, rs, h + c0, rows, nullptr, tup, prec, st);
                 if (rc) return rc;
                 cudaError_t e = launch_search(rs.d_desc, uint32_t(rs.host.tuples.size()), cw, h + c0, tup, rows,
-                                              ids + c0, stats, tune ? tune->search_mode : 0, st);
+                                              ids + c0, stats, tune, st);
                 if (e != cudaSuccess) return set_err(ctx, TANG_EDEVICE, "search: %s", cudaGetErrorString(e));
             }
             return TANG_OK;
@@ -414,6 +414,7 @@ static int enqueue_classify(tang_ctx *ctx, Ruleset &rs, const tang_header *h, ui
 
 static int classify_host(tang_ctx *ctx, Ruleset &rs, const tang_header *h, uint32_t n, uint32_t *ids, uint32_t path,
                          DevStats *stats);
+
 
 int tang_classify(tang_ctx *ctx, uint32_t rsh, const tang_header *headers, uint32_t n, uint32_t *ids, uint32_t flags,
                   void *stream, tang_stats *stats) {
@@ -605,8 +606,8 @@ int tang_search(tang_ctx *ctx, uint32_t rsh, const tang_header *d_headers, const
     if (rs->has_update) CK(cudaStreamWaitEvent(st, rs->last_update, 0));
     DevStats *dst = stats ? ctx->d_stats : nullptr;
     if (dst) CK(cudaMemsetAsync(dst, 0, sizeof(DevStats), st));
-    CK(launch_search(rs->d_desc, uint32_t(rs->host.tuples.size()), rs->host.cw, d_headers, d_tuple, n, d_ids, dst, 0,
-                     st));
+    CK(launch_search(rs->d_desc, uint32_t(rs->host.tuples.size()), rs->host.cw, d_headers, d_tuple, n, d_ids, dst,
+                     nullptr, st));
     if (stats) {
         DevStats hs;
         CK(cudaMemcpyAsync(&hs, dst, sizeof(hs), cudaMemcpyDeviceToHost, st));
@@ -653,3 +654,15 @@ double tang_now(void) {
 }
 
 }  // extern "C"
+
+namespace tang {
+// Device-resident classification of one batch on `st` (serving engine, autotuner).
+int enqueue_classify_path(tang_ctx *ctx, uint32_t rsh, const tang_header *h, uint32_t n, uint32_t *ids, uint32_t path,
+                          cudaStream_t st) {
+    Ruleset *rs = find_rs(ctx, rsh);
+    if (!rs) return set_err(ctx, TANG_ENOTFOUND, "unknown ruleset %u", rsh);
+    if (rs->has_update) CK(cudaStreamWaitEvent(st, rs->last_update, 0));
+    return enqueue_classify(ctx, *rs, h, n, ids, path, nullptr, st);
+}
+void drop_graphs_of(tang_ctx *ctx) { drop_graphs(ctx); }
+}  // namespace tang

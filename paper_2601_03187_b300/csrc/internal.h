@@ -142,11 +142,12 @@ struct GraphKey {
     bool operator<(const GraphKey &o) const;
 };
 
+// Launch shape chosen by the autotuner per (ruleset, path); zeros mean "default".
 struct TuneEntry {
-    int ctas_per_sm = 1;
-    int search_mode = 0;   // 0 thread-per-packet, 1 warp-cooperative
-    int grid_mult = 1;
-    float ms = 0.f;
+    int search_threads = 0;  // threads per block of the search kernel (128 / 256 / 512)
+    int search_bps = 0;      // resident blocks per SM the search grid is sized for
+    int fused_grid = 0;      // persistent CTAs of the fused kernel (0 = one per SM)
+    float ms = 0.f;          // best time measured by the tuner
 };
 
 struct Ruleset {
@@ -224,7 +225,7 @@ cudaError_t launch_conflict_insert(const Tables *d_desc, uint32_t pool_size, uin
 cudaError_t launch_run_shift(DRule *pool, uint32_t start, uint32_t len, uint32_t pos, int dir, cudaStream_t st);
 cudaError_t launch_run_copy(DRule *pool, uint32_t from, uint32_t to, uint32_t len, cudaStream_t st);
 cudaError_t launch_search(const Tables *d_desc, uint32_t T, uint32_t cw, const tang_header *h,
-                          const int32_t *tuple, uint32_t n, uint32_t *ids, DevStats *stats, int mode,
+                          const int32_t *tuple, uint32_t n, uint32_t *ids, DevStats *stats, const TuneEntry *tune,
                           cudaStream_t st);
 
 // mlp_simt.cu (FP32 CUDA-core kernels: plain path and trainer)

@@ -674,7 +674,6 @@ int tc_prepare_model(tang_ctx *ctx, DeviceModel &m) {
 int tc_launch(tang_ctx *ctx, Ruleset &rs, const tang_header *h, uint32_t n, uint32_t *ids, float *logits,
               int32_t *tuple, int precision, bool fused_search, DevStats *stats, cudaStream_t st,
               const TuneEntry *tune) {
-    (void)tune;
     if (n == 0) return TANG_OK;
     DeviceModel &m = *rs.model;
     const bool f8 = precision == TANG_FP8;
@@ -707,7 +706,8 @@ int tc_launch(tang_ctx *ctx, Ruleset &rs, const tang_header *h, uint32_t n, uint
     prm.C = m.C;
     prm.Cpad = m.Cpad;
     prm.fused_search = fused_search && ids ? 1 : 0;
-    const uint32_t grid = std::min<uint32_t>(prm.n_tiles, uint32_t(ctx->sm_count));
+    uint32_t grid = uint32_t(tune && tune->fused_grid > 0 ? tune->fused_grid : ctx->sm_count);
+    grid = std::min<uint32_t>(prm.n_tiles, std::min<uint32_t>(grid, uint32_t(ctx->sm_count)));
     if (f8)
         k_tc_classify<true><<<grid, tc::kThreads, tc::kSmemBytes, st>>>(maps->hid, maps->out, prm);
     else

@@ -68,7 +68,7 @@ extern "C" int tang_classify_noalloc(tang_ctx *ctx, uint32_t rsh, const tang_hea
     rc = tc_launch(ctx, rs, d_headers, n, nullptr, nullptr, tuples, TANG_BF16, false, nullptr, st, nullptr);
     if (rc) return rc;
     cudaError_t e = launch_search(rs.d_desc, uint32_t(rs.host.tuples.size()), rs.host.cw, d_headers, tuples, n, d_ids,
-                                  nullptr, 0, st);
+                                  nullptr, nullptr, st);
     if (e != cudaSuccess) return set_err(ctx, TANG_EDEVICE, "search: %s", cudaGetErrorString(e));
     return TANG_OK;
 }

@@ -14,8 +14,8 @@ __device__ __forceinline__ void warp_add(unsigned long long *dst, uint32_t v) {
 
 // One thread per packet; grid-stride. Tuple descriptors and the search order are staged in
 // shared memory (T <= 64), so a probe costs one slot load plus one 32-byte load per rule read.
-template <bool STATS>
-__global__ void __launch_bounds__(256) k_search(const Tables *__restrict__ desc, const tang_header *__restrict__ hdr,
+template <int THREADS, bool STATS>
+__global__ void __launch_bounds__(THREADS) k_search(const Tables *__restrict__ desc, const tang_header *__restrict__ hdr,
                                                 const int32_t *__restrict__ pred, uint32_t n,
                                                 uint32_t *__restrict__ ids, DevStats *stats) {
     __shared__ TupleDesc s_tuples[kSmemTuples];
@@ -63,21 +63,31 @@ __global__ void __launch_bounds__(256) k_search(const Tables *__restrict__ desc,
 }
 
 cudaError_t launch_search(const Tables *d_desc, uint32_t T, uint32_t cw, const tang_header *h, const int32_t *tuple,
-                          uint32_t n, uint32_t *ids, DevStats *stats, int mode, cudaStream_t st) {
+                          uint32_t n, uint32_t *ids, DevStats *stats, const TuneEntry *tune, cudaStream_t st) {
     (void)T;
     (void)cw;
-    (void)mode;
     if (n == 0) return cudaSuccess;
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    uint32_t blocks = (n + 255) / 256;
-    uint32_t cap = uint32_t(sms) * 8;  // 8 resident blocks of 256 threads per SM
+    const int threads = tune && tune->search_threads ? tune->search_threads : 256;
+    const int bps = tune && tune->search_bps ? tune->search_bps : 8;
+    uint32_t blocks = (n + threads - 1) / threads;
+    const uint32_t cap = uint32_t(sms) * uint32_t(bps);
     if (blocks > cap) blocks = cap;
-    if (stats)
-        k_search<true><<<blocks, 256, 0, st>>>(d_desc, h, tuple, n, ids, stats);
-    else
-        k_search<false><<<blocks, 256, 0, st>>>(d_desc, h, tuple, n, ids, stats);
+#define TANG_SEARCH_LAUNCH(TH)                                                                     \
+    if (stats)                                                                                     \
+        k_search<TH, true><<<blocks, TH, 0, st>>>(d_desc, h, tuple, n, ids, stats);                 \
+    else                                                                                           \
+        k_search<TH, false><<<blocks, TH, 0, st>>>(d_desc, h, tuple, n, ids, stats);
+    if (threads == 128) {
+        TANG_SEARCH_LAUNCH(128)
+    } else if (threads == 512) {
+        TANG_SEARCH_LAUNCH(512)
+    } else {
+        TANG_SEARCH_LAUNCH(256)
+    }
+#undef TANG_SEARCH_LAUNCH
     return cudaGetLastError();
 }
 

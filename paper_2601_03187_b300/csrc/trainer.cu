@@ -273,7 +273,7 @@ int train_run(tang_ctx *ctx, Ruleset &rs, const tang_header *samples, uint32_t n
         }
         std::vector<uint32_t> ids(hs.size());
         cudaMemcpyAsync(dh, hs.data(), sizeof(tang_header) * hs.size(), cudaMemcpyHostToDevice, st);
-        launch_search(rs.d_desc, T, rs.host.cw, dh, nullptr, uint32_t(hs.size()), di, nullptr, 0, st);
+        launch_search(rs.d_desc, T, rs.host.cw, dh, nullptr, uint32_t(hs.size()), di, nullptr, nullptr, st);
         cudaMemcpyAsync(ids.data(), di, 4 * hs.size(), cudaMemcpyDeviceToHost, st);
         cudaError_t e = cudaStreamSynchronize(st);
         ctx_free(ctx, dh);

@@ -208,3 +208,29 @@ def test_updates_stay_exact(ctx):
         ctx.insert_rule(rs, cur[0])  # id already live
     assert ctx.suboptimal_count(rs) >= 0
     ctx.unload_ruleset(rs)
+
+
+def test_graph_replay_sees_updates_after_table_growth(ctx):
+    """A graph captured before many inserts (which relocate runs, grow the rule pool and rehash
+    tuple tables) replays correctly afterwards: kernels read the tables through a descriptor."""
+    rules = wl.rules_for_config(0, n_rules=800)
+    rs = ctx.load_ruleset(rules)
+    h = wl.trace_for_config(0, rules, seed=4)[:20000]
+    d = to_dev(h)
+    ids = ids_dev(len(h))
+    for _ in range(2):
+        ctx.classify(rs, d, ids, path="no_nn", graph=True)
+    torch.cuda.synchronize()
+    assert (ids_host(ids) == oc.classify(rules, h)).all()
+    fresh = wl.gen_rules(6000, 77)
+    fresh["id"] += 10 ** 6
+    fresh["priority"] = np.random.default_rng(1).integers(0, 800, len(fresh))
+    for r in fresh:
+        ctx.insert_rule(rs, r)
+    info = ctx.ruleset_info(rs)
+    assert info["n_rules"] == 6800
+    ctx.classify(rs, d, ids, path="no_nn", graph=True)  # replay of the graph captured above
+    torch.cuda.synchronize()
+    cur = np.concatenate([rules, fresh])
+    assert (ids_host(ids) == oc.classify(cur, h)).all()
+    ctx.unload_ruleset(rs)
