@@ -279,6 +279,8 @@ def main():
     ap.add_argument("--train-seconds", type=float, default=float(os.environ.get("TANG_TRAIN_SECONDS", "20")))
     ap.add_argument("--quick", action="store_true", help="skip the secondary measurements")
     ap.add_argument("--packets", type=int, default=N_PACKETS, help="use the first P packets of the trace")
+    ap.add_argument("--variant", default=None, choices=[None, "1sm", "2sm"],
+                    help="tensor-core kernel variant (default: the library's choice)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
     world, rank, local = dist_setup()
@@ -315,13 +317,13 @@ def main():
 
     def time_path(path, steps, warmup, graph=True):
         for _ in range(warmup):
-            ctx.classify(rs, d_h, ids, path=path, graph=graph)
+            ctx.classify(rs, d_h, ids, path=path, graph=graph, variant=args.variant)
         torch.cuda.synchronize()
         barrier(world)
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
         for _ in range(steps):
-            ctx.classify(rs, d_h, ids, path=path, graph=graph)
+            ctx.classify(rs, d_h, ids, path=path, graph=graph, variant=args.variant)
         ev1.record(stream)
         torch.cuda.synchronize()
         barrier(world)
@@ -333,7 +335,7 @@ def main():
     dt = max_over_ranks(dt, world)
     value = world * n * args.steps / dt / 1e6
     ids_fused = ids.cpu().numpy().view(np.uint32)
-    st_bf16 = ctx.classify(rs, d_h, ids, path="fused_bf16", stats=True)
+    st_bf16 = ctx.classify(rs, d_h, ids, path="fused_bf16", stats=True, variant=args.variant)
 
     fpp = flops_per_packet(T)
     ms_launch = dt / args.steps * 1e3

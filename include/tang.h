@@ -181,6 +181,14 @@ int tang_load_model(tang_ctx *ctx, uint32_t rs, const void *blob, size_t bytes);
 /* Other flags. */
 #define TANG_GRAPH 0x100          /* DEVICE mode: capture the launch sequence in a CUDA graph
                                      keyed by (ruleset, path, n, pointers, stream) and replay it */
+/* Tensor-core kernel variant (fused and staged paths, and tang_infer's precision argument);
+ * neither bit = the autotuned choice, else the library default. */
+#define TANG_FUSED_1SM 0x200      /* one CTA per SM, M = 128 packets, 128-wide MMAs, 2 accumulators */
+#define TANG_FUSED_2SM 0x400      /* CTA pairs (cta_group::2), M = 256 packets per MMA */
+#define TANG_FUSED_MCAST2 0x800   /* 1-SM MMAs; clusters of 2 CTAs share each weight tile (TMA multicast) */
+#define TANG_FUSED_MCAST4 0x1000  /* same with clusters of 4 CTAs */
+#define TANG_FUSED_N256 0x2000    /* one CTA per SM, 256-wide MMAs, single-buffered accumulator */
+#define TANG_VARIANT_MASK 0x3E00
 
 typedef struct tang_stats {
     uint64_t packets;       /* packets classified */
@@ -205,7 +213,8 @@ int tang_classify(tang_ctx *ctx, uint32_t rs, const tang_header *headers, uint32
 /* Stage 1 alone (§4.1.1): run the network of ruleset rs over n device headers.
  * d_logits (device, n x C float, row-major; may be NULL) receives the output layer's logits;
  * d_tuple (device, n int32; may be NULL) the argmax (lowest index on ties).
- * precision: TANG_FP32 / TANG_BF16 / TANG_FP8. Asynchronous on `stream`. */
+ * precision: TANG_FP32 / TANG_BF16 / TANG_FP8, optionally OR-ed with TANG_FUSED_1SM or
+ * TANG_FUSED_2SM to pick the tensor-core kernel variant. Asynchronous on `stream`. */
 int tang_infer(tang_ctx *ctx, uint32_t rs, const tang_header *d_headers, uint32_t n, float *d_logits,
                int32_t *d_tuple, int precision, void *stream);
 

@@ -15,7 +15,7 @@ import numpy as np
 from workloads import HEADER_DTYPE, RULE_DTYPE
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libtang.so")
+LIB_PATH = os.environ.get("TANG_LIBRARY") or os.path.join(_HERE, "libtang.so")
 
 # constants of include/tang.h
 NO_MATCH = 0xFFFFFFFF
@@ -27,6 +27,8 @@ PATHS = {
     "staged_bf16": PATH_STAGED_BF16, "no_nn": PATH_NO_NN, "staged_fp8": PATH_STAGED_FP8,
 }
 MEM_DEVICE, MEM_HOST, GRAPH = 0x00, 0x10, 0x100
+FUSED_1SM, FUSED_2SM, FUSED_MCAST2, FUSED_MCAST4, FUSED_N256 = 0x200, 0x400, 0x800, 0x1000, 0x2000
+VARIANTS = {None: 0, "1sm": FUSED_1SM, "2sm": FUSED_2SM, "mc2": FUSED_MCAST2, "mc4": FUSED_MCAST4, "n256": FUSED_N256}
 MODEL_MAGIC = 0x474E4154
 MODEL_HEADER_BYTES = 64
 
@@ -286,10 +288,11 @@ class Context:
         self._ck(lib.tang_load_model(self._h, rs, buf, len(blob)), "load_model")
 
     # -- classification ---------------------------------------------------------------------
-    def classify(self, rs: int, headers, ids, path="fused_bf16", graph=False, stream=None, stats=False):
-        """ids[i] = matching rule id. numpy headers/ids -> host mode; torch CUDA tensors -> device mode."""
+    def classify(self, rs: int, headers, ids, path="fused_bf16", graph=False, stream=None, stats=False, variant=None):
+        """ids[i] = matching rule id. numpy headers/ids -> host mode; torch CUDA tensors -> device mode.
+        variant: None (tuned / default), "1sm" or "2sm" tensor-core kernel."""
         host = isinstance(headers, np.ndarray)
-        flags = PATHS[path] if isinstance(path, str) else int(path)
+        flags = (PATHS[path] if isinstance(path, str) else int(path)) | VARIANTS[variant]
         flags |= MEM_HOST if host else MEM_DEVICE
         if graph:
             flags |= GRAPH
@@ -300,10 +303,10 @@ class Context:
                                    ctypes.byref(st) if stats else None), "classify")
         return st.as_dict() if stats else None
 
-    def infer(self, rs: int, headers, logits=None, tuples=None, precision=BF16, stream=None):
+    def infer(self, rs: int, headers, logits=None, tuples=None, precision=BF16, stream=None, variant=None):
         n = _n_headers(headers)
-        self._ck(lib.tang_infer(self._h, rs, _ptr(headers), n, _ptr(logits), _ptr(tuples), precision,
-                                _stream(stream)), "infer")
+        self._ck(lib.tang_infer(self._h, rs, _ptr(headers), n, _ptr(logits), _ptr(tuples),
+                                precision | VARIANTS[variant], _stream(stream)), "infer")
 
     def search(self, rs: int, headers, tuples, ids, stream=None, stats=False):
         n = _n_headers(headers)

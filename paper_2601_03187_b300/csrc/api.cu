@@ -99,6 +99,17 @@ static int check_device_error(tang_ctx *ctx) {
     return TANG_OK;
 }
 
+// Kernel variant requested by flag bits: 1 = 1-SM N=128, 2 = 2-SM pairs, 3 / 4 = 1-SM with weight
+// tiles multicast across clusters of 2 / 4 CTAs, 5 = 1-SM N=256, 0 = tuned or library default.
+static int variant_of(uint32_t flags) {
+    if (flags & TANG_FUSED_N256) return 5;
+    if (flags & TANG_FUSED_2SM) return 2;
+    if (flags & TANG_FUSED_MCAST4) return 4;
+    if (flags & TANG_FUSED_MCAST2) return 3;
+    if (flags & TANG_FUSED_1SM) return 1;
+    return 0;
+}
+
 static Ruleset *find_rs(tang_ctx *ctx, uint32_t rs) {
     auto it = ctx->rulesets.find(rs);
     return it == ctx->rulesets.end() ? nullptr : it->second.get();
@@ -271,6 +282,9 @@ void tang_model_free(tang_ctx *ctx, DeviceModel *m) {
     ctx_free(ctx, m->d_bias_tc);
     free(m->tmap_bf16);
     free(m->tmap_fp8);
+    free(m->tmap2_bf16);
+    free(m->tmap2_fp8);
+    free(m->tmap256);
     m->d_params = nullptr;
 }
 
@@ -299,7 +313,7 @@ int tang_load_model(tang_ctx *ctx, uint32_t rsh, const void *blob, size_t bytes)
     m->N = hd.N;
     m->blocks = hd.blocks;
     m->C = hd.C;
-    m->Cpad = std::max<uint32_t>(16, (hd.C + 15) / 16 * 16);
+    m->Cpad = std::max<uint32_t>(32, (hd.C + 31) / 32 * 32);
     const float *amax = reinterpret_cast<const float *>(static_cast<const uint8_t *>(blob) + sizeof(hd));
     bool calibrated = true;
     for (size_t i = 0; i < n_amax; ++i) {
@@ -349,18 +363,21 @@ int tang_load_model(tang_ctx *ctx, uint32_t rsh, const void *blob, size_t bytes)
 // Classification
 // ---------------------------------------------------------------------------------------
 static int run_infer(tang_ctx *ctx, Ruleset &rs, const tang_header *h, uint32_t n, float *logits, int32_t *tuple,
-                     int precision, cudaStream_t st) {
+                     int precision, cudaStream_t st, int variant = 0) {
     if (!rs.model) return set_err(ctx, TANG_EINVAL, "ruleset %u has no model", rs.handle);
     if (precision == TANG_FP32) return mlp_fp32_forward(ctx, *rs.model, h, n, logits, tuple, st);
     if (!rs.model->d_wbf16) return set_err(ctx, TANG_EUNSUPPORTED, "tensor-core path needs N == 512 and C <= 256");
     if (precision == TANG_FP8 && !rs.model->has_fp8)
         return set_err(ctx, TANG_EINVAL, "FP8 path needs a calibrated model (act_amax)");
-    return tc_launch(ctx, rs, h, n, nullptr, logits, tuple, precision, false, nullptr, st, nullptr);
+    const TuneEntry *tune = nullptr;
+    auto it = rs.tune.find(precision == TANG_FP8 ? TANG_PATH_STAGED_FP8 : TANG_PATH_STAGED_BF16);
+    if (it != rs.tune.end()) tune = &it->second;
+    return tc_launch(ctx, rs, h, n, nullptr, logits, tuple, precision, false, nullptr, st, tune, variant);
 }
 
 // Enqueue the device-resident classification of one batch on `st` (no synchronisation).
 static int enqueue_classify(tang_ctx *ctx, Ruleset &rs, const tang_header *h, uint32_t n, uint32_t *ids,
-                            uint32_t path, DevStats *stats, cudaStream_t st) {
+                            uint32_t path, DevStats *stats, cudaStream_t st, int variant = 0) {
     if (n == 0) return TANG_OK;
     const int cw = int(rs.host.cw);
     const TuneEntry *tune = nullptr;
@@ -390,7 +407,7 @@ static int enqueue_classify(tang_ctx *ctx, Ruleset &rs, const tang_header *h, ui
                 int rc = ensure_scratch(ctx, off + size_t(chunk) * sizeof(int32_t));
                 if (rc) return rc;
                 int32_t *tup = reinterpret_cast<int32_t *>(static_cast<uint8_t *>(ctx->scratch) + off);
-                rc = run_infer(ctx, rs, h + c0, rows, nullptr, tup, prec, st);
+                rc = run_infer(ctx, rs, h + c0, rows, nullptr, tup, prec, st, variant);
                 if (rc) return rc;
                 cudaError_t e = launch_search(rs.d_desc, uint32_t(rs.host.tuples.size()), cw, h + c0, tup, rows,
                                               ids + c0, stats, tune, st);
@@ -405,7 +422,7 @@ static int enqueue_classify(tang_ctx *ctx, Ruleset &rs, const tang_header *h, ui
             const int prec = path == TANG_PATH_FUSED_BF16 ? TANG_BF16 : TANG_FP8;
             if (prec == TANG_FP8 && !rs.model->has_fp8)
                 return set_err(ctx, TANG_EINVAL, "FP8 path needs a calibrated model (act_amax)");
-            return tc_launch(ctx, rs, h, n, ids, nullptr, nullptr, prec, true, stats, st, tune);
+            return tc_launch(ctx, rs, h, n, ids, nullptr, nullptr, prec, true, stats, st, tune, variant);
         }
         default:
             return set_err(ctx, TANG_EINVAL, "unknown path %u", path);
@@ -413,7 +430,7 @@ static int enqueue_classify(tang_ctx *ctx, Ruleset &rs, const tang_header *h, ui
 }
 
 static int classify_host(tang_ctx *ctx, Ruleset &rs, const tang_header *h, uint32_t n, uint32_t *ids, uint32_t path,
-                         DevStats *stats);
+                         DevStats *stats, int variant);
 
 
 int tang_classify(tang_ctx *ctx, uint32_t rsh, const tang_header *headers, uint32_t n, uint32_t *ids, uint32_t flags,
@@ -425,29 +442,30 @@ int tang_classify(tang_ctx *ctx, uint32_t rsh, const tang_header *headers, uint3
     if ((reinterpret_cast<uintptr_t>(headers) & 15) || (reinterpret_cast<uintptr_t>(ids) & 3))
         return set_err(ctx, TANG_EINVAL, "headers must be 16-byte aligned and ids 4-byte aligned");
     const uint32_t path = flags & TANG_PATH_MASK;
+    const int variant = variant_of(flags);
     cudaSetDevice(ctx->device);
     cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : ctx->stream;
     DevStats *dst = stats ? ctx->d_stats : nullptr;
     if (dst) CK(cudaMemsetAsync(dst, 0, sizeof(DevStats), st));
     int rc;
     if (flags & TANG_MEM_HOST) {
-        rc = classify_host(ctx, *rs, headers, n, ids, path, dst);
+        rc = classify_host(ctx, *rs, headers, n, ids, path, dst, variant);
     } else {
         if (rs->has_update) CK(cudaStreamWaitEvent(st, rs->last_update, 0));
         if ((flags & TANG_GRAPH) && !dst && n) {
-            GraphKey key{rsh, path, n, headers, ids, (void *)st};
+            GraphKey key{rsh, path | uint32_t(variant) << 8, n, headers, ids, (void *)st};
             auto it = ctx->graphs.find(key);
             if (it == ctx->graphs.end()) {
                 // First call for this key: run eagerly (this sizes any scratch, so nothing
                 // allocates or synchronises inside the capture), then capture for later calls.
-                rc = enqueue_classify(ctx, *rs, headers, n, ids, path, nullptr, st);
+                rc = enqueue_classify(ctx, *rs, headers, n, ids, path, nullptr, st, variant);
                 if (rc) return rc;
                 CK(cudaStreamSynchronize(st));
                 // capture on a private stream so the caller's stream may be the legacy one
                 cudaStream_t cap;
                 CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
                 CK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
-                rc = enqueue_classify(ctx, *rs, headers, n, ids, path, nullptr, cap);
+                rc = enqueue_classify(ctx, *rs, headers, n, ids, path, nullptr, cap, variant);
                 cudaGraph_t g = nullptr;
                 cudaError_t e = cudaStreamEndCapture(cap, &g);
                 cudaStreamDestroy(cap);
@@ -466,7 +484,7 @@ int tang_classify(tang_ctx *ctx, uint32_t rsh, const tang_header *headers, uint3
             }
             rc = TANG_OK;
         } else {
-            rc = enqueue_classify(ctx, *rs, headers, n, ids, path, dst, st);
+            rc = enqueue_classify(ctx, *rs, headers, n, ids, path, dst, st, variant);
         }
     }
     if (rc) return rc;
@@ -491,7 +509,7 @@ int tang_classify(tang_ctx *ctx, uint32_t rsh, const tang_header *headers, uint3
 // D2H (copy_out stream) through two device buffers, so copies of one chunk overlap the
 // compute of the next. Pageable user buffers are staged through pinned buffers by this thread.
 static int classify_host(tang_ctx *ctx, Ruleset &rs, const tang_header *h, uint32_t n, uint32_t *ids, uint32_t path,
-                         DevStats *stats) {
+                         DevStats *stats, int variant) {
     if (n == 0) return TANG_OK;
     const uint32_t chunk = std::min<uint32_t>(n, 1u << 20);
     if (ctx->dev_pkts < chunk) {
@@ -556,7 +574,8 @@ static int classify_host(tang_ctx *ctx, Ruleset &rs, const tang_header *h, uint3
         cudaMemcpyAsync(dh + size_t(b) * chunk, src, sizeof(tang_header) * rows, cudaMemcpyHostToDevice, ctx->copy_in);
         cudaEventRecord(ev_in[b], ctx->copy_in);
         cudaStreamWaitEvent(ctx->stream, ev_in[b], 0);
-        rc = enqueue_classify(ctx, rs, dh + size_t(b) * chunk, rows, di + size_t(b) * chunk, path, stats, ctx->stream);
+        rc = enqueue_classify(ctx, rs, dh + size_t(b) * chunk, rows, di + size_t(b) * chunk, path, stats, ctx->stream,
+                              variant);
         cudaEventRecord(ev_comp[b], ctx->stream);
         cudaStreamWaitEvent(ctx->copy_out, ev_comp[b], 0);
         uint32_t *dst = pinned ? ids + c0 : pi + size_t(b) * chunk;
@@ -591,7 +610,8 @@ int tang_infer(tang_ctx *ctx, uint32_t rsh, const tang_header *d_headers, uint32
     if (!d_headers || (reinterpret_cast<uintptr_t>(d_headers) & 15)) return set_err(ctx, TANG_EINVAL, "bad headers");
     cudaSetDevice(ctx->device);
     cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : ctx->stream;
-    return run_infer(ctx, *rs, d_headers, n, d_logits, d_tuple, precision, st);
+    const int variant = variant_of(uint32_t(precision));
+    return run_infer(ctx, *rs, d_headers, n, d_logits, d_tuple, precision & 0xF, st, variant);
 }
 
 int tang_search(tang_ctx *ctx, uint32_t rsh, const tang_header *d_headers, const int32_t *d_tuple, uint32_t n,

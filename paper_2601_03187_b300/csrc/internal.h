@@ -127,8 +127,11 @@ struct DeviceModel {
     float act_amax[64] = {0};
     bool has_fp8 = false;
     float act_scale[64] = {0};        // FP8 activation scale per tensor-core layer input
-    void *tmap_bf16 = nullptr;        // host-side CUtensorMap blobs (128 B each), see mlp_tc.cu
+    void *tmap_bf16 = nullptr;        // host-side CUtensorMap pairs, see tc_common.cuh (1-SM kernel)
     void *tmap_fp8 = nullptr;
+    void *tmap2_bf16 = nullptr;       // half-tile maps of the 2-SM kernel
+    void *tmap2_fp8 = nullptr;
+    void *tmap256 = nullptr;          // 256-row maps of the N=256 kernel: [BF16, FP8]
 };
 
 struct Ruleset;
@@ -147,6 +150,7 @@ struct TuneEntry {
     int search_threads = 0;  // threads per block of the search kernel (128 / 256 / 512)
     int search_bps = 0;      // resident blocks per SM the search grid is sized for
     int fused_grid = 0;      // persistent CTAs of the fused kernel (0 = one per SM)
+    int fused_variant = 0;   // 1 = 1-SM kernel, 2 = 2-SM pair kernel, 0 = library default
     float ms = 0.f;          // best time measured by the tuner
 };
 
@@ -241,7 +245,9 @@ int mlp_fp32_forward(tang_ctx *ctx, const DeviceModel &m, const tang_header *h, 
 int tc_prepare_model(tang_ctx *ctx, DeviceModel &m);
 int tc_launch(tang_ctx *ctx, Ruleset &rs, const tang_header *h, uint32_t n, uint32_t *ids, float *logits,
               int32_t *tuple, int precision, bool fused_search, DevStats *stats, cudaStream_t st,
-              const TuneEntry *tune);
+              const TuneEntry *tune, int variant);
+int tc2_prepare_model(tang_ctx *ctx, DeviceModel &m);
+int tc256_prepare_model(tang_ctx *ctx, DeviceModel &m);
 
 // trainer.cu
 int train_run(tang_ctx *ctx, Ruleset &rs, const tang_header *samples, uint32_t n, const tang_train_cfg &cfg,

@@ -25,9 +25,13 @@
 #include <cuda_fp8.h>
 
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <vector>
 #include <cstring>
 
 #include "search_dev.cuh"
+#include "tc_common.cuh"
 #include "tc_ptx.cuh"
 
 namespace tang {
@@ -59,38 +63,9 @@ constexpr int kOffMisc = kOffBar + kNumBars * 8;
 constexpr int kSmemBytes = kOffMisc + 16 + 1024;  // + alignment slack
 }  // namespace tc
 
-struct TcParams {
-    const tang_header *headers;
-    uint32_t n, n_tiles;
-    uint32_t *ids;
-    float *logits;
-    int32_t *tuple;
-    const Tables *tables;
-    DevStats *stats;
-    int *err;
-    const float *W0, *b0;   // FP32 layer 0: W0[7][512], b0[512]
-    const float *bias;      // [12][512] hidden biases, then [Cpad] output biases
-    const float *dq;        // FP8 only: per layer and output column 1 / (act scale * weight scale)
-    const float *sa;        // FP8 only: [13] activation scales of the layers' inputs
-    uint32_t C, Cpad;
-    int fused_search;
-};
-
-__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
-    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
-    return *reinterpret_cast<uint32_t *>(&v);
-}
-__device__ __forceinline__ uint32_t pack_e4m3x4(float a, float b, float c, float d) {
-    const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(a, b), __NV_SATFINITE, __NV_E4M3);
-    const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(c, d), __NV_SATFINITE, __NV_E4M3);
-    return (lo & 0xFFFFu) | (hi << 16);
-}
-__device__ __forceinline__ float e4m3_to_f(uint32_t byte) {
-    __half_raw h = __nv_cvt_fp8_to_halfraw(__nv_fp8_storage_t(byte), __NV_E4M3);
-    return __half2float(__half(h));
-}
-
-template <bool F8>
+// CS = CTAs per cluster that share every weight tile: each loads 1/CS of the tile's rows and
+// multicasts them to all, so L2 serves each weight line once per cluster instead of once per SM.
+template <bool F8, int CS>
 __global__ void __launch_bounds__(tc::kThreads, 1)
     k_tc_classify(const __grid_constant__ CUtensorMap tm_hid, const __grid_constant__ CUtensorMap tm_out,
                   const TcParams p) {
@@ -116,11 +91,17 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
     constexpr int KB = F8 ? 4 : 8;                 // K-blocks (128-byte rows) per 512-wide layer input
     constexpr int KBW = F8 ? 128 : 64;             // elements per K-block
     constexpr uint32_t kActArrivals = F8 ? 8 : 4;  // epilogue warps writing one K-block
+    constexpr uint16_t kMask = uint16_t((1u << CS) - 1);
+    const uint32_t crank = CS > 1 ? ptx::cluster_ctarank() : 0;
+    // every CTA of a cluster runs the same number of tile rounds (the weight pipeline is shared);
+    // rounds past the end run on masked rows
+    const uint32_t cbase = blockIdx.x - crank;
+    auto round_live = [&](uint32_t k) { return cbase + k * gridDim.x < p.n_tiles; };
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
             ptx::mbar_init(&full[s], 1);
-            ptx::mbar_init(&empty[s], 1);
+            ptx::mbar_init(&empty[s], CS);
         }
         for (int b = 0; b < 2; ++b) {
             ptx::mbar_init(&acc_full[b], 1);
@@ -151,7 +132,10 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
         ptx::tmem_relinquish();
     }
     ptx::tc_fence_before();
-    __syncthreads();
+    if (CS > 1)
+        ptx::cluster_sync();  // every CTA's barriers exist before multicast loads and commits land
+    else
+        __syncthreads();
     ptx::tc_fence_after();
     const uint32_t tmem = *sTmem;
 
@@ -163,9 +147,10 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
     if (warp == kWarpProd) {
         // ---------------- TMA producer ----------------
         if (lane == 0) {
-            uint32_t stage = 0, phase = 0;
+            uint32_t stage = 0, phase = 0, n_loads = 0;
             bool ok = true;
-            for (uint32_t tile = blockIdx.x; tile < p.n_tiles && ok; tile += gridDim.x) {
+            const uint32_t hid_rows = 128 / CS, out_rows = p.Cpad / CS;
+            for (uint32_t k = 0; round_live(k) && ok; ++k) {
                 for (int L = 0; L <= kLayers && ok; ++L) {
                     const int nch = L == kLayers ? 1 : 4;
                     for (int c = 0; c < nch && ok; ++c)
@@ -175,13 +160,23 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
                                 ok = false;
                                 break;
                             }
+                            TC_TRACE(trace::kProd + n_loads, n_loads < trace::kLoads);
+                            ++n_loads;
+                            uint8_t *dst = sStage + stage * kStageBytes;
                             if (L < kLayers) {
                                 ptx::mbar_arrive_expect_tx(&full[stage], kStageBytes);
-                                ptx::tma_load_2d(sStage + stage * kStageBytes, &tm_hid, &full[stage], kb * KBW,
-                                                 L * kHid + c * 128);
+                                if (CS == 1)
+                                    ptx::tma_load_2d(dst, &tm_hid, &full[stage], kb * KBW, L * kHid + c * 128);
+                                else
+                                    ptx::tma_load_2d_mc(dst + crank * hid_rows * 128, &tm_hid, &full[stage], kb * KBW,
+                                                        L * kHid + c * 128 + int(crank * hid_rows), kMask);
                             } else {
                                 ptx::mbar_arrive_expect_tx(&full[stage], p.Cpad * 128);
-                                ptx::tma_load_2d(sStage + stage * kStageBytes, &tm_out, &full[stage], kb * KBW, 0);
+                                if (CS == 1)
+                                    ptx::tma_load_2d(dst, &tm_out, &full[stage], kb * KBW, 0);
+                                else
+                                    ptx::tma_load_2d_mc(dst + crank * out_rows * 128, &tm_out, &full[stage], kb * KBW,
+                                                        int(crank * out_rows), kMask);
                             }
                             if (++stage == kStages) {
                                 stage = 0;
@@ -207,18 +202,21 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
             const uint32_t y_addr = ptx::smem_u32(sY), st_addr = ptx::smem_u32(sStage);
             uint32_t stage = 0, phase = 0, acc_cnt = 0, lay = 0;
             bool ok = true;
-            for (uint32_t tile = blockIdx.x; tile < p.n_tiles && ok; tile += gridDim.x) {
+            for (uint32_t k = 0; round_live(k) && ok; ++k) {
                 for (int L = 0; L <= kLayers && ok; ++L, ++lay) {
                     const bool a_tmem = (L & 1) == 0;  // FC1 and output layer read x from TMEM
                     const int nch = L == kLayers ? 1 : 4;
                     const uint32_t idesc = L == kLayers ? idesc_o : idesc_h;
                     for (int c = 0; c < nch && ok; ++c, ++acc_cnt) {
                         const uint32_t buf = acc_cnt & 1, use = acc_cnt >> 1;
+                        const bool tr = acc_cnt < uint32_t(trace::kChunks);
+                        TC_TRACE(trace::kMma + acc_cnt * 12 + 0, tr);
                         if (use > 0 && !ptx::mbar_wait(&acc_empty[buf], (use - 1) & 1, sAbort, kTimeoutNs)) {
                             fail(2);
                             ok = false;
                             break;
                         }
+                        TC_TRACE(trace::kMma + acc_cnt * 12 + 1, tr);
                         ptx::tc_fence_after();
                         const uint32_t d = tmem + buf * 128;
                         for (int kb = 0; kb < KB; ++kb) {
@@ -232,6 +230,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
                                 ok = false;
                                 break;
                             }
+                            TC_TRACE(trace::kMma + acc_cnt * 12 + 2 + kb, tr);
                             ptx::tc_fence_after();
                             const uint32_t b_base = st_addr + stage * kStageBytes;
 #pragma unroll
@@ -243,7 +242,10 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
                                 else
                                     ptx::mma_ss(d, ptx::sdesc_sw128(y_addr + kb * 16384 + kk * 32), bd, idesc, accum, F8);
                             }
-                            ptx::mma_commit(&empty[stage]);
+                            if (CS == 1)
+                                ptx::mma_commit(&empty[stage]);
+                            else
+                                ptx::mma_commit_mc(&empty[stage], kMask);  // the stage is free in every CTA
                             if (++stage == kStages) {
                                 stage = 0;
                                 phase ^= 1;
@@ -251,6 +253,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
                         }
                         if (!ok) break;
                         ptx::mma_commit(&acc_full[buf]);
+                        TC_TRACE(trace::kMma + acc_cnt * 12 + 10, tr);
                     }
                 }
             }
@@ -296,8 +299,9 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
             if (lane == 0) ptx::mbar_arrive(&act[col0 / KBW]);
         };
 
-        for (uint32_t tile = blockIdx.x; tile < p.n_tiles && ok; tile += gridDim.x) {
-            const uint32_t i = tile * kM + r;
+        for (uint32_t k = 0; round_live(k) && ok; ++k) {
+            const uint32_t tile = blockIdx.x + k * gridDim.x;
+            const uint32_t i = tile < p.n_tiles ? tile * kM + r : 0xFFFFFFFFu;
             float f[7];
             {
                 uint4 v = i < p.n ? __ldg(reinterpret_cast<const uint4 *>(p.headers + i)) : make_uint4(0, 0, 0, 0);
@@ -351,11 +355,15 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
                 const float s_res = F8 ? 1.f / sa[L - (fc2 ? 1 : 0)] : 1.f;
                 for (int c = 0; c < 4; ++c, ++acc_cnt) {
                     const uint32_t buf = acc_cnt & 1, use = acc_cnt >> 1;
+                    const bool tr = lane == 0 && (ew & 3) == 0 && acc_cnt < uint32_t(trace::kChunks);
+                    const int tslot = trace::kEpi + ((ew >> 2) * trace::kChunks + int(acc_cnt)) * 4;
+                    TC_TRACE(tslot + 0, tr);
                     if (!ptx::mbar_wait(&acc_full[buf], use & 1, sAbort, kTimeoutNs)) {
                         fail(16);
                         ok = false;
                         break;
                     }
+                    TC_TRACE(tslot + 1, tr);
                     ptx::tc_fence_after();
                     const int unit = 2 * c + hc;
 #pragma unroll
@@ -375,6 +383,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
                             ptx::tc_fence_before();
                             __syncwarp();
                             if (lane == 0) ptx::mbar_arrive(&acc_empty[buf]);
+                            TC_TRACE(tslot + 2, tr);
                         }
                         float v[32];
 #pragma unroll
@@ -424,6 +433,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
                     else
                         ptx::fence_proxy_async_smem();
                     act_arrive(unit * 64);
+                    TC_TRACE(tslot + 3, tr);
                 }
             }
             if (!ok) break;
@@ -496,7 +506,8 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
             uint32_t tcnt = 0;
             uint32_t st_pk = 0, st_match = 0, st_correct = 0, st_hit = 0, st_fb = 0;
             Counters cn{0, 0, 0};
-            for (uint32_t tile = blockIdx.x; tile < p.n_tiles; tile += gridDim.x) {
+            for (uint32_t k = 0; round_live(k); ++k) {
+                const uint32_t tile = blockIdx.x + k * gridDim.x;
                 const uint32_t t = tcnt & 1, tu = tcnt >> 1;
                 ++tcnt;
                 if (!ptx::mbar_wait(&tfull[t], tu & 1, sAbort, kTimeoutNs)) {
@@ -507,7 +518,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
                 __syncwarp();
                 if (lane == 0) ptx::mbar_arrive(&tempty[t]);
                 const uint32_t i = tile * kM + r;
-                if (i < p.n) {
+                if (tile < p.n_tiles && i < p.n) {
                     const Hdr h = load_header(p.headers + i);
                     Best best;
                     const bool hit = search_packet(tb, tuples, order, h, pred, best, cn);
@@ -540,7 +551,10 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
     }
 
     ptx::tc_fence_before();
-    __syncthreads();
+    if (CS > 1)
+        ptx::cluster_sync();  // no CTA leaves while peers may still multicast into it or commit to it
+    else
+        __syncthreads();
     ptx::tc_fence_after();
     if (warp == kWarpMma) ptx::tmem_dealloc(tmem, 512);
 }
@@ -566,7 +580,7 @@ static EncodeTiledFn encode_fn() {
 }
 
 // Row-major [rows][512] matrix of 1- or 2-byte elements, box = 128 bytes x box_rows, 128B swizzle.
-static int make_tmap(tang_ctx *ctx, CUtensorMap *m, void *base, uint32_t rows, bool f8, uint32_t box_rows) {
+int make_tmap(tang_ctx *ctx, CUtensorMap *m, void *base, uint32_t rows, bool f8, uint32_t box_rows) {
     EncodeTiledFn enc = encode_fn();
     if (!enc) return set_err(ctx, TANG_EDEVICE, "cuTensorMapEncodeTiled unavailable");
     const uint32_t esz = f8 ? 1 : 2;
@@ -580,10 +594,6 @@ static int make_tmap(tang_ctx *ctx, CUtensorMap *m, void *base, uint32_t rows, b
     if (r != CUDA_SUCCESS) return set_err(ctx, TANG_EDEVICE, "cuTensorMapEncodeTiled failed (%d)", int(r));
     return TANG_OK;
 }
-
-struct TcMaps {
-    CUtensorMap hid, out;
-};
 
 // Derive the tensor-core copies of a model: transposed (K-major) BF16 weights, FP8 weights with
 // per-output-channel scales, FP32 biases, FP8 dequantisation factors and activation scales.
@@ -628,10 +638,16 @@ int tc_prepare_model(tang_ctx *ctx, DeviceModel &m) {
     if (rc) return rc;
     cudaMemcpy(m.d_wbf16, wb.data(), wb.size() * 2, cudaMemcpyHostToDevice);
     cudaMemcpy(m.d_bias_tc, bias.data(), bias.size() * 4, cudaMemcpyHostToDevice);
-    TcMaps *maps = static_cast<TcMaps *>(aligned_alloc(64, sizeof(TcMaps)));
+    // one map pair per cluster size 1, 2, 4: a CTA loads 128/CS rows of each hidden tile and
+    // Cpad/CS rows of each output tile
+    TcMaps *maps = static_cast<TcMaps *>(aligned_alloc(64, 3 * sizeof(TcMaps)));
     m.tmap_bf16 = maps;
-    if ((rc = make_tmap(ctx, &maps->hid, m.d_wbf16, tc::kLayers * N, false, 128))) return rc;
-    if ((rc = make_tmap(ctx, &maps->out, static_cast<__nv_bfloat16 *>(m.d_wbf16) + hid, Cpad, false, Cpad))) return rc;
+    for (int ci = 0; ci < 3; ++ci) {
+        const uint32_t cs = 1u << ci;
+        if ((rc = make_tmap(ctx, &maps[ci].hid, m.d_wbf16, tc::kLayers * N, false, 128 / cs))) return rc;
+        if ((rc = make_tmap(ctx, &maps[ci].out, static_cast<__nv_bfloat16 *>(m.d_wbf16) + hid, Cpad, false, Cpad / cs)))
+            return rc;
+    }
 
     if (m.has_fp8) {
         // activation scale: the power of two that maps the calibrated max |x| into (224, 448]
@@ -661,33 +677,86 @@ int tc_prepare_model(tang_ctx *ctx, DeviceModel &m) {
         cudaMemcpy(m.d_wscale8, dq.data(), dq.size() * 4, cudaMemcpyHostToDevice);
         // the 13 activation scales follow the dequantisation factors
         cudaMemcpy(m.d_wscale8 + dq.size(), m.act_scale, 13 * 4, cudaMemcpyHostToDevice);
-        TcMaps *m8 = static_cast<TcMaps *>(aligned_alloc(64, sizeof(TcMaps)));
+        TcMaps *m8 = static_cast<TcMaps *>(aligned_alloc(64, 3 * sizeof(TcMaps)));
         m.tmap_fp8 = m8;
-        if ((rc = make_tmap(ctx, &m8->hid, m.d_wfp8, tc::kLayers * N, true, 128))) return rc;
-        if ((rc = make_tmap(ctx, &m8->out, static_cast<uint8_t *>(m.d_wfp8) + hid, Cpad, true, Cpad))) return rc;
+        for (int ci = 0; ci < 3; ++ci) {
+            const uint32_t cs = 1u << ci;
+            if ((rc = make_tmap(ctx, &m8[ci].hid, m.d_wfp8, tc::kLayers * N, true, 128 / cs))) return rc;
+            if ((rc = make_tmap(ctx, &m8[ci].out, static_cast<uint8_t *>(m.d_wfp8) + hid, Cpad, true, Cpad / cs)))
+                return rc;
+        }
     }
+    if ((rc = tc2_prepare_model(ctx, m))) return rc;
+    if ((rc = tc256_prepare_model(ctx, m))) return rc;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return set_err(ctx, TANG_EDEVICE, "tc_prepare_model: %s", cudaGetErrorString(e));
     return TANG_OK;
 }
 
+int tc2_launch(tang_ctx *ctx, DeviceModel &m, const TcParams &prm, bool f8, cudaStream_t st, int grid_cap);
+int tc256_launch(tang_ctx *ctx, DeviceModel &m, const TcParams &prm, bool f8, cudaStream_t st, int grid_cap);
+
+// Launch the 1-SM kernel in clusters of CS CTAs: as many clusters as fit on the device at once
+// (one CTA per SM), capped by the tile count and the tuned grid.
+template <bool F8, int CS>
+static int launch_1sm(tang_ctx *ctx, const TcMaps &maps, const TcParams &prm, cudaStream_t st, const TuneEntry *tune) {
+    static bool init = false;
+    static int max_clusters = 0;
+    if (!init) {
+        cudaError_t e = cudaFuncSetAttribute(k_tc_classify<F8, CS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             tc::kSmemBytes);
+        if (e != cudaSuccess) return set_err(ctx, TANG_EDEVICE, "smem attribute: %s", cudaGetErrorString(e));
+        max_clusters = ctx->sm_count / CS;
+        if (CS > 1) {
+            cudaLaunchConfig_t q = {};
+            q.gridDim = dim3(CS * (ctx->sm_count / CS), 1, 1);
+            q.blockDim = dim3(tc::kThreads, 1, 1);
+            q.dynamicSmemBytes = tc::kSmemBytes;
+            cudaLaunchAttribute qa[1];
+            qa[0].id = cudaLaunchAttributeClusterDimension;
+            qa[0].val.clusterDim.x = CS;
+            qa[0].val.clusterDim.y = 1;
+            qa[0].val.clusterDim.z = 1;
+            q.attrs = qa;
+            q.numAttrs = 1;
+            int c = 0;
+            if (cudaOccupancyMaxActiveClusters(&c, k_tc_classify<F8, CS>, &q) == cudaSuccess && c > 0)
+                max_clusters = std::min(max_clusters, c);
+            cudaGetLastError();
+        }
+        init = true;
+    }
+    uint32_t clusters = uint32_t(max_clusters);
+    if (tune && tune->fused_grid > 0) clusters = std::min<uint32_t>(clusters, uint32_t(tune->fused_grid / CS));
+    clusters = std::max<uint32_t>(1, std::min<uint32_t>(clusters, (prm.n_tiles + CS - 1) / CS));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(CS * clusters, 1, 1);
+    cfg.blockDim = dim3(tc::kThreads, 1, 1);
+    cfg.dynamicSmemBytes = tc::kSmemBytes;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = CS;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, k_tc_classify<F8, CS>, maps.hid, maps.out, prm);
+    if (e != cudaSuccess) return set_err(ctx, TANG_EDEVICE, "tc kernel launch: %s", cudaGetErrorString(e));
+    return TANG_OK;
+}
+
+// Library default variant when neither the caller nor the tuner chose one.
+constexpr int kDefaultVariant = 5;  // N=256 kernel (mlp_tc256.cu)
+
 int tc_launch(tang_ctx *ctx, Ruleset &rs, const tang_header *h, uint32_t n, uint32_t *ids, float *logits,
               int32_t *tuple, int precision, bool fused_search, DevStats *stats, cudaStream_t st,
-              const TuneEntry *tune) {
+              const TuneEntry *tune, int variant) {
     if (n == 0) return TANG_OK;
     DeviceModel &m = *rs.model;
     const bool f8 = precision == TANG_FP8;
     const TcMaps *maps = static_cast<const TcMaps *>(f8 ? m.tmap_fp8 : m.tmap_bf16);
     if (!maps) return set_err(ctx, TANG_EUNSUPPORTED, "no tensor-core copy of this model");
-    static bool attr_done[2] = {false, false};
-    if (!attr_done[f8]) {
-        cudaError_t e = f8 ? cudaFuncSetAttribute(k_tc_classify<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                  tc::kSmemBytes)
-                           : cudaFuncSetAttribute(k_tc_classify<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                  tc::kSmemBytes);
-        if (e != cudaSuccess) return set_err(ctx, TANG_EDEVICE, "smem attribute: %s", cudaGetErrorString(e));
-        attr_done[f8] = true;
-    }
     TcParams prm{};
     prm.headers = h;
     prm.n = n;
@@ -706,14 +775,36 @@ int tc_launch(tang_ctx *ctx, Ruleset &rs, const tang_header *h, uint32_t n, uint
     prm.C = m.C;
     prm.Cpad = m.Cpad;
     prm.fused_search = fused_search && ids ? 1 : 0;
-    uint32_t grid = uint32_t(tune && tune->fused_grid > 0 ? tune->fused_grid : ctx->sm_count);
-    grid = std::min<uint32_t>(prm.n_tiles, std::min<uint32_t>(grid, uint32_t(ctx->sm_count)));
-    if (f8)
-        k_tc_classify<true><<<grid, tc::kThreads, tc::kSmemBytes, st>>>(maps->hid, maps->out, prm);
-    else
-        k_tc_classify<false><<<grid, tc::kThreads, tc::kSmemBytes, st>>>(maps->hid, maps->out, prm);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return set_err(ctx, TANG_EDEVICE, "tc kernel launch: %s", cudaGetErrorString(e));
+    prm.trace = nullptr;
+#ifdef TANG_TC_TRACE
+    static unsigned long long *d_trace = nullptr;
+    if (!d_trace) cudaMalloc(&d_trace, sizeof(unsigned long long) * trace::kTotal);
+    cudaMemsetAsync(d_trace, 0, sizeof(unsigned long long) * trace::kTotal, st);
+    prm.trace = d_trace;
+#endif
+    const int v = variant ? variant : (tune && tune->fused_variant ? tune->fused_variant : kDefaultVariant);
+    if (v == 2 || v == 5) {
+        const int rc = v == 2 ? tc2_launch(ctx, m, prm, f8, st, tune ? tune->fused_grid : 0)
+                              : tc256_launch(ctx, m, prm, f8, st, tune ? tune->fused_grid : 0);
+        if (rc != TANG_EUNSUPPORTED) return rc;  // models without those maps run the 1-SM N=128 kernel
+    }
+    // variants 1, 3, 4: the 1-SM kernel with weight tiles shared by clusters of 1, 2, 4 CTAs
+    const int ci = v == 3 ? 1 : v == 4 ? 2 : 0;
+    int rc = ci == 0 ? (f8 ? launch_1sm<true, 1>(ctx, maps[0], prm, st, tune) : launch_1sm<false, 1>(ctx, maps[0], prm, st, tune))
+             : ci == 1 ? (f8 ? launch_1sm<true, 2>(ctx, maps[1], prm, st, tune) : launch_1sm<false, 2>(ctx, maps[1], prm, st, tune))
+                       : (f8 ? launch_1sm<true, 4>(ctx, maps[2], prm, st, tune) : launch_1sm<false, 4>(ctx, maps[2], prm, st, tune));
+    if (rc) return rc;
+#ifdef TANG_TC_TRACE
+    if (const char *path = getenv("TANG_TC_TRACE_FILE")) {
+        std::vector<unsigned long long> hbuf(trace::kTotal);
+        cudaMemcpyAsync(hbuf.data(), d_trace, sizeof(unsigned long long) * trace::kTotal, cudaMemcpyDeviceToHost, st);
+        cudaStreamSynchronize(st);
+        if (FILE *f = fopen(path, "wb")) {
+            fwrite(hbuf.data(), sizeof(unsigned long long), hbuf.size(), f);
+            fclose(f);
+        }
+    }
+#endif
     return TANG_OK;
 }
 

@@ -65,7 +65,7 @@ extern "C" int tang_classify_noalloc(tang_ctx *ctx, uint32_t rsh, const tang_hea
         return set_err(ctx, TANG_EDEVICE, "cudaStreamWaitEvent failed");
     // every entry below n is written by the network kernel before the search kernel reads it,
     // so the array needs no clearing between calls
-    rc = tc_launch(ctx, rs, d_headers, n, nullptr, nullptr, tuples, TANG_BF16, false, nullptr, st, nullptr);
+    rc = tc_launch(ctx, rs, d_headers, n, nullptr, nullptr, tuples, TANG_BF16, false, nullptr, st, nullptr, 0);
     if (rc) return rc;
     cudaError_t e = launch_search(rs.d_desc, uint32_t(rs.host.tuples.size()), rs.host.cw, d_headers, tuples, n, d_ids,
                                   nullptr, nullptr, st);

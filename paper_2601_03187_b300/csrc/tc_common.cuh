@@ -1,0 +1,80 @@
+// Pieces shared by the tensor-core kernels (1-SM and 2-SM variants).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+
+#include "internal.h"
+
+namespace tang {
+
+struct TcParams {
+    const tang_header *headers;
+    uint32_t n, n_tiles;
+    uint32_t *ids;
+    float *logits;
+    int32_t *tuple;
+    const Tables *tables;
+    DevStats *stats;
+    int *err;
+    const float *W0, *b0;   // FP32 layer 0: W0[7][512], b0[512]
+    const float *bias;      // [12][512] hidden biases, then [Cpad] output biases
+    const float *dq;        // FP8 only: per layer and output column 1 / (act scale * weight scale)
+    const float *sa;        // FP8 only: [13] activation scales of the layers' inputs
+    uint32_t C, Cpad;
+    int fused_search;
+    unsigned long long *trace;  // event timestamps of CTA 0 (trace builds only, else null)
+};
+
+// Optional event trace (built with -DTANG_TC_TRACE): clock64() stamps of CTA 0 at fixed slots.
+namespace trace {
+constexpr int kChunks = 100;                   // first 100 accumulator chunks (about two tiles)
+constexpr int kMma = 0;                        // [chunk][12]: start, acc_empty ok, full ok x8, issued
+constexpr int kEpi = kMma + kChunks * 12;      // [warp 0/1][chunk][4]: wait, acc_full ok, drained, published
+constexpr int kProd = kEpi + 2 * kChunks * 4;  // [load]: empty ok
+constexpr int kLoads = 800;
+constexpr int kTotal = kProd + kLoads;
+}  // namespace trace
+#ifdef TANG_TC_TRACE
+#define TC_TRACE(slot, limit)                                                        \
+    do {                                                                            \
+        if (p.trace && blockIdx.x == 0 && (limit)) p.trace[(slot)] = clock64();     \
+    } while (0)
+// 2-SM kernel: CTAs 0 and 1 (the first pair), each in its own kTotal-sized region
+#define TC_TRACE2(slot, limit)                                                                   \
+    do {                                                                                        \
+        if (p.trace && blockIdx.x < 2 && (limit)) p.trace[blockIdx.x * trace::kTotal + (slot)] = clock64(); \
+    } while (0)
+#else
+#define TC_TRACE2(slot, limit) \
+    do {                       \
+    } while (0)
+#define TC_TRACE(slot, limit) \
+    do {                      \
+    } while (0)
+#endif
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t *>(&v);
+}
+__device__ __forceinline__ uint32_t pack_e4m3x4(float a, float b, float c, float d) {
+    const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(a, b), __NV_SATFINITE, __NV_E4M3);
+    const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(c, d), __NV_SATFINITE, __NV_E4M3);
+    return (lo & 0xFFFFu) | (hi << 16);
+}
+__device__ __forceinline__ float e4m3_to_f(uint32_t byte) {
+    __half_raw h = __nv_cvt_fp8_to_halfraw(__nv_fp8_storage_t(byte), __NV_E4M3);
+    return __half2float(__half(h));
+}
+
+struct TcMaps {
+    CUtensorMap hid, out;
+};
+
+// Row-major [rows][512] weight matrix of 1- or 2-byte elements as a TMA tensor map whose box is
+// 128 bytes x box_rows with 128-byte swizzle.
+int make_tmap(tang_ctx *ctx, CUtensorMap *m, void *base, uint32_t rows, bool f8, uint32_t box_rows);
+
+}  // namespace tang

@@ -60,23 +60,24 @@ def e4m3_weights(p64):
     return q
 
 
-def infer(ctx, rs, h, C, precision):
+def infer(ctx, rs, h, C, precision, variant=None):
     d = to_dev(h)
     z = torch.zeros((len(h), C), dtype=torch.float32, device="cuda")
     t = torch.zeros(len(h), dtype=torch.int32, device="cuda")
-    ctx.infer(rs, d, z, t, precision=precision)
+    ctx.infer(rs, d, z, t, precision=precision, variant=variant)
     torch.cuda.synchronize()
     return z.cpu().numpy().astype(np.float64), t.cpu().numpy()
 
 
+@pytest.mark.parametrize("variant", ["1sm", "2sm", "mc2", "mc4", "n256"])
 @pytest.mark.parametrize("prec", ["bf16", "fp8"])
-def test_logits_within_bound(setup, prec):
+def test_logits_within_bound(setup, prec, variant):
     ctx, rules, rs, T, p, p64, h = setup
     hs = h[:4096]
     X = mlp.features(hs)
     q = bf16_weights(p64) if prec == "bf16" else e4m3_weights(p64)
     z64 = mlp.forward(q, X)
-    z, tup = infer(ctx, rs, hs, T, tg.BF16 if prec == "bf16" else tg.FP8)
+    z, tup = infer(ctx, rs, hs, T, tg.BF16 if prec == "bf16" else tg.FP8, variant)
     tol = logit_tolerance(q, X, U32, U_BF16 if prec == "bf16" else U_E4M3)
     err = np.abs(z - z64)
     assert np.isfinite(z).all()
@@ -87,32 +88,34 @@ def test_logits_within_bound(setup, prec):
     assert np.median(rel) < (0.02 if prec == "bf16" else 0.3)
 
 
+@pytest.mark.parametrize("variant", ["1sm", "2sm", "mc2", "mc4", "n256"])
 @pytest.mark.parametrize("path", ["fused_bf16", "staged_bf16", "fused_fp8", "staged_fp8"])
-def test_ids_exact(setup, path):
+def test_ids_exact(setup, path, variant):
     ctx, rules, rs, T, p, p64, h = setup
     want = oc.classify(rules, h)
     d = to_dev(h)
     ids = ids_dev(len(h))
-    st = ctx.classify(rs, d, ids, path=path, stats=True)
+    st = ctx.classify(rs, d, ids, path=path, stats=True, variant=variant)
     assert (ids_host(ids) == want).all()
     assert st["packets"] == len(h)
     assert st["pred_hit"] + st["fallback"] == len(h)
 
 
-def test_ragged_sizes_and_graph(setup):
+@pytest.mark.parametrize("variant", ["1sm", "2sm", "mc2", "mc4", "n256"])
+def test_ragged_sizes_and_graph(setup, variant):
     ctx, rules, rs, T, p, p64, h = setup
-    for n in (1, 5, 127, 128, 129, 1000, 148 * 128 + 3):
+    for n in (1, 5, 127, 128, 129, 255, 256, 257, 1000, 148 * 128 + 3, 74 * 256 + 129):
         hs = h[:n]
         d = to_dev(hs)
         ids = ids_dev(n)
-        ctx.classify(rs, d, ids, path="fused_bf16")
+        ctx.classify(rs, d, ids, path="fused_bf16", variant=variant)
         torch.cuda.synchronize()
         assert (ids_host(ids) == oc.classify(rules, hs)).all(), n
     d = to_dev(h)
     want = oc.classify(rules, h)
     for _ in range(3):
         ids = ids_dev(len(h))
-        ctx.classify(rs, d, ids, path="fused_bf16", graph=True)
+        ctx.classify(rs, d, ids, path="fused_bf16", graph=True, variant=variant)
         torch.cuda.synchronize()
         assert (ids_host(ids) == want).all()
 
@@ -122,5 +125,11 @@ def test_predictions_agree_across_precisions(setup):
     ctx, rules, rs, T, p, p64, h = setup
     hs = h[:20000]
     _, t32 = infer(ctx, rs, hs, T, tg.FP32)
-    _, t16 = infer(ctx, rs, hs, T, tg.BF16)
+    _, t16 = infer(ctx, rs, hs, T, tg.BF16, "1sm")
     assert (t32 == t16).mean() > 0.9
+    # every tensor-core variant runs the same arithmetic on each row
+    z16 = infer(ctx, rs, hs, T, tg.BF16, "1sm")[0]
+    for v in ("2sm", "mc2", "mc4", "n256"):
+        zv, tv = infer(ctx, rs, hs, T, tg.BF16, v)
+        assert (tv == t16).all(), v
+        assert (zv == z16).all(), v
