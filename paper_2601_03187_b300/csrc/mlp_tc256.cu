@@ -126,7 +126,7 @@ __global__ void __maxnreg__(96)
 
     if (warp == kWarpProd) {
         if (lane == 0) {
-            uint32_t stage = 0, phase = 0;
+            uint32_t stage = 0, phase = 0, n_loads = 0;
             bool ok = true;
             for (uint32_t tile = blockIdx.x; tile < p.n_tiles && ok; tile += gridDim.x) {
                 for (int L = 0; L <= kLayers && ok; ++L) {
@@ -138,6 +138,8 @@ __global__ void __maxnreg__(96)
                                 ok = false;
                                 break;
                             }
+                            TC_TRACE(trace::kProd + n_loads, n_loads < trace::kLoads);
+                            ++n_loads;
                             uint8_t *dst = sStage + stage * kStageBytes;
                             if (L < kLayers) {
                                 ptx::mbar_arrive_expect_tx(&full[stage], kStageBytes);
@@ -172,11 +174,14 @@ __global__ void __maxnreg__(96)
                     const int nch = L == kLayers ? 1 : 2;
                     const uint32_t idesc = L == kLayers ? idesc_o : idesc_h;
                     for (int c = 0; c < nch && ok; ++c, ++uses) {
+                        const bool tr = uses < uint32_t(trace::kChunks);
+                        TC_TRACE(trace::kMma + uses * 12 + 0, tr);
                         if (uses > 0 && !ptx::mbar_wait(acc_empty, (uses - 1) & 1, sAbort, kTimeoutNs)) {
                             fail(2);
                             ok = false;
                             break;
                         }
+                        TC_TRACE(trace::kMma + uses * 12 + 1, tr);
                         ptx::tc_fence_after();
                         for (int kb = 0; kb < KB; ++kb) {
                             if (c == 0 && !ptx::mbar_wait(&act[kb], lay & 1, sAbort, kTimeoutNs)) {
@@ -189,6 +194,7 @@ __global__ void __maxnreg__(96)
                                 ok = false;
                                 break;
                             }
+                            TC_TRACE(trace::kMma + uses * 12 + 2 + kb, tr);
                             ptx::tc_fence_after();
                             const uint32_t b_base = st_addr + stage * kStageBytes;
 #pragma unroll
@@ -208,6 +214,7 @@ __global__ void __maxnreg__(96)
                         }
                         if (!ok) break;
                         ptx::mma_commit(acc_full);
+                        TC_TRACE(trace::kMma + uses * 12 + 10, tr);
                     }
                 }
             }
@@ -312,11 +319,15 @@ __global__ void __maxnreg__(96)
                 const float s_out = F8 ? sa[L + 1] : 1.f;
                 const float s_res = F8 ? 1.f / sa[fc2 ? L - 1 : L] : 1.f;
                 for (int c = 0; c < 2; ++c, ++uses) {
+                    const bool tr = lane == 0 && q == 2 && g < 2 && uses < uint32_t(trace::kChunks);
+                    const int tslot = trace::kEpi + (g * trace::kChunks + int(uses)) * 4;
+                    TC_TRACE(tslot + 0, tr);
                     if (!ptx::mbar_wait(acc_full, uses & 1, sAbort, kTimeoutNs)) {
                         fail(16);
                         ok = false;
                         break;
                     }
+                    TC_TRACE(tslot + 1, tr);
                     ptx::tc_fence_after();
                     const int unit = 4 * c + g;
                     uint32_t a0[32], a1[32];
@@ -327,6 +338,7 @@ __global__ void __maxnreg__(96)
                     ptx::tc_fence_before();
                     __syncwarp();
                     if (lane == 0) ptx::mbar_arrive(acc_empty);
+                    TC_TRACE(tslot + 2, tr);
 #pragma unroll
                     for (int s = 0; s < 2; ++s) {
                         const int col0 = unit * 64 + s * 32;
@@ -364,6 +376,7 @@ __global__ void __maxnreg__(96)
                     else
                         ptx::fence_proxy_async_smem();
                     act_arrive(unit * 64);
+                    TC_TRACE(tslot + 3, tr);
                 }
             }
             if (!ok) break;
@@ -512,12 +525,30 @@ int tc256_launch(tang_ctx *ctx, DeviceModel &m, const TcParams &prm, bool f8, cu
     }
     uint32_t grid = uint32_t(grid_cap > 0 ? grid_cap : ctx->sm_count);
     grid = std::min<uint32_t>(prm.n_tiles, std::min<uint32_t>(grid, uint32_t(ctx->sm_count)));
+    TcParams prm_t = prm;
+#ifdef TANG_TC_TRACE
+    static unsigned long long *d_trace = nullptr;
+    if (!d_trace) cudaMalloc(&d_trace, sizeof(unsigned long long) * trace::kTotal);
+    cudaMemsetAsync(d_trace, 0, sizeof(unsigned long long) * trace::kTotal, st);
+    prm_t.trace = d_trace;
+#endif
     if (f8)
-        k_tc256_classify<true><<<grid, tc256::kThreads, tc256::kSmemBytes, st>>>(maps.hid, maps.out, prm);
+        k_tc256_classify<true><<<grid, tc256::kThreads, tc256::kSmemBytes, st>>>(maps.hid, maps.out, prm_t);
     else
-        k_tc256_classify<false><<<grid, tc256::kThreads, tc256::kSmemBytes, st>>>(maps.hid, maps.out, prm);
+        k_tc256_classify<false><<<grid, tc256::kThreads, tc256::kSmemBytes, st>>>(maps.hid, maps.out, prm_t);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return set_err(ctx, TANG_EDEVICE, "N=256 kernel launch: %s", cudaGetErrorString(e));
+#ifdef TANG_TC_TRACE
+    if (const char *path = getenv("TANG_TC_TRACE_FILE")) {
+        std::vector<unsigned long long> hbuf(trace::kTotal);
+        cudaMemcpyAsync(hbuf.data(), d_trace, sizeof(unsigned long long) * hbuf.size(), cudaMemcpyDeviceToHost, st);
+        cudaStreamSynchronize(st);
+        if (FILE *f = fopen(path, "wb")) {
+            fwrite(hbuf.data(), sizeof(unsigned long long), hbuf.size(), f);
+            fclose(f);
+        }
+    }
+#endif
     return TANG_OK;
 }
 
