@@ -280,6 +280,8 @@ void tang_model_free(tang_ctx *ctx, DeviceModel *m) {
     ctx_free(ctx, m->d_wfp8);
     ctx_free(ctx, m->d_wscale8);
     ctx_free(ctx, m->d_bias_tc);
+    ctx_free(ctx, m->d_fold8);
+    ctx_free(ctx, m->d_l0);
     free(m->tmap_bf16);
     free(m->tmap_fp8);
     free(m->tmap2_bf16);

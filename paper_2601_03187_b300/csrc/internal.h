@@ -124,6 +124,12 @@ struct DeviceModel {
     void *d_wfp8 = nullptr;           // E4M3 bytes, per-output-channel scaled
     float *d_wscale8 = nullptr;       // per layer, per output channel: 1 / weight scale
     float *d_bias_tc = nullptr;       // per layer N (or Cpad) biases, FP32, output layer last
+    // N=256 FP8 kernel: per hidden layer l, dq[l][n] * s[l+1], then bias[l][n] * s[l+1], with s the
+    // power-of-two activation scale of the layer's output (so the products are exact)
+    float *d_fold8 = nullptr;
+    // N=256 kernel: layer 0 as a K=64 BF16 contraction, [2][512][64] (unscaled, then times the
+    // FP8 input scale s[0]); see tc256_prepare_model
+    void *d_l0 = nullptr;
     float act_amax[64] = {0};
     bool has_fp8 = false;
     float act_scale[64] = {0};        // FP8 activation scale per tensor-core layer input

@@ -580,12 +580,12 @@ static EncodeTiledFn encode_fn() {
 }
 
 // Row-major [rows][512] matrix of 1- or 2-byte elements, box = 128 bytes x box_rows, 128B swizzle.
-int make_tmap(tang_ctx *ctx, CUtensorMap *m, void *base, uint32_t rows, bool f8, uint32_t box_rows) {
+int make_tmap(tang_ctx *ctx, CUtensorMap *m, void *base, uint32_t rows, bool f8, uint32_t box_rows, uint32_t cols) {
     EncodeTiledFn enc = encode_fn();
     if (!enc) return set_err(ctx, TANG_EDEVICE, "cuTensorMapEncodeTiled unavailable");
     const uint32_t esz = f8 ? 1 : 2;
-    cuuint64_t dims[2] = {512, rows};
-    cuuint64_t strides[1] = {512 * esz};
+    cuuint64_t dims[2] = {cols, rows};
+    cuuint64_t strides[1] = {cols * esz};
     cuuint32_t box[2] = {128 / esz, box_rows};
     cuuint32_t es[2] = {1, 1};
     CUresult r = enc(m, f8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box,
@@ -677,6 +677,16 @@ int tc_prepare_model(tang_ctx *ctx, DeviceModel &m) {
         cudaMemcpy(m.d_wscale8, dq.data(), dq.size() * 4, cudaMemcpyHostToDevice);
         // the 13 activation scales follow the dequantisation factors
         cudaMemcpy(m.d_wscale8 + dq.size(), m.act_scale, 13 * 4, cudaMemcpyHostToDevice);
+        // the output scale s[l+1] folded into each hidden layer's dequantisation factor and bias;
+        // s is a power of two, so relu(s * (acc * dq + b)) is bit-identical to the unfolded form
+        std::vector<float> fold(size_t(2) * tc::kLayers * N);
+        for (int l = 0; l < tc::kLayers; ++l)
+            for (uint32_t n = 0; n < N; ++n) {
+                fold[size_t(l) * N + n] = dq[size_t(l) * N + n] * m.act_scale[l + 1];
+                fold[size_t(tc::kLayers + l) * N + n] = bias[size_t(l) * N + n] * m.act_scale[l + 1];
+            }
+        if ((rc = ctx_alloc(ctx, fold.size() * 4, (void **)&m.d_fold8))) return rc;
+        cudaMemcpy(m.d_fold8, fold.data(), fold.size() * 4, cudaMemcpyHostToDevice);
         TcMaps *m8 = static_cast<TcMaps *>(aligned_alloc(64, 3 * sizeof(TcMaps)));
         m.tmap_fp8 = m8;
         for (int ci = 0; ci < 3; ++ci) {
@@ -772,6 +782,7 @@ int tc_launch(tang_ctx *ctx, Ruleset &rs, const tang_header *h, uint32_t n, uint
     prm.bias = m.d_bias_tc;
     prm.dq = f8 ? m.d_wscale8 : nullptr;
     prm.sa = f8 ? m.d_wscale8 + size_t(tc::kLayers) * m.N + m.Cpad : nullptr;
+    prm.fold8 = f8 ? m.d_fold8 : nullptr;
     prm.C = m.C;
     prm.Cpad = m.Cpad;
     prm.fused_search = fused_search && ids ? 1 : 0;

@@ -9,11 +9,26 @@
 // release the accumulator at once; bias, residual, ReLU, quantisation and the operand stores
 // then overlap the next chunk's MMAs.
 //
-// Per tile (128 packets): layer 0 on CUDA cores -> x (TMEM); per block: FC1 in two 256-column
-// chunks (A = x from TMEM) -> u (swizzled shared memory); FC2 in two chunks (A = u from shared
-// memory) -> x = ReLU(acc + b2 + x) in place (Eq. 1); output FC (N = Cpad) + argmax; the exact
-// search of §4.1.1 on 2 search warps. Weight tiles are 256 rows x 128 bytes (32 KB), streamed by
-// TMA through two stages. All waits are bounded (2 s of %globaltimer) as in the other kernels.
+// Per tile (128 packets): layer 0 on the tensor core -> x (TMEM); per block: FC1 in two
+// 256-column chunks (A = x from TMEM) -> u (swizzled shared memory); FC2 in two chunks (A = u
+// from shared memory) -> x = ReLU(acc + b2 + x) in place (Eq. 1); output FC (N = Cpad) + argmax;
+// the exact search of §4.1.1 on 2 search warps.
+//
+// Layer 0 (7 header fields -> 512, FP32 in the other kernels) is one K=48 BF16 contraction per
+// 256 columns with FP32 accumulation: every 16-bit field f splits exactly into bytes,
+// f = 256 * hi + lo, and every weight and bias into three BF16 parts w1 + w2 + w3 that carry its
+// 24 significant bits, so A = [hi(7), lo(7)] x 3 parts, 1 x 3 bias parts, and all products are
+// exact. The sum matches the FP32 one up to accumulation order (a few units in the last FP32
+// place), far below the BF16 / E4M3 rounding applied next. On CUDA cores the same layer costs a
+// uniform broadcast per weight per warp, about 9k cycles per tile at one broadcast per cycle.
+//
+// Weight tiles are 256 rows x 128 bytes (32 KB), streamed by TMA through three stages (BF16) or
+// four (FP8, whose u buffer is half the size), so that at a chunk boundary the next chunk's first
+// K-blocks are already in flight while the accumulator changes hands. The epilogue spends few
+// instructions per element: vector bias loads, ReLU folded into the packing conversion, and for
+// FP8 the output scale folded into the per-column constants (exact, the scales being powers of
+// two) and two-at-a-time E4M3 decoding of the residual. All waits are bounded (2 s of
+// %globaltimer) as in the other kernels.
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -29,52 +44,71 @@ namespace tc256 {
 constexpr int kM = 128;
 constexpr int kHid = 512;
 constexpr int kLayers = 12;
-constexpr int kStages = 2;
 constexpr int kStageBytes = 32768;  // 256 rows x 128 bytes
 constexpr int kNumEpiWarps = 16;
-constexpr int kWarpProd = 0, kWarpMma = 1, kWarpEpi = 2, kWarpSearch = kWarpEpi + kNumEpiWarps, kNumSearchWarps = 2;
-constexpr int kThreads = 32 * (kWarpSearch + kNumSearchWarps);  // 640
+// Warp groups (4 warps each): 0 = producer (warp 0) and MMA issuer (warp 1); 1..4 = the epilogue;
+// 5 = the search. Every sub-partition gets one warp of each group.
+constexpr int kWarpProd = 0, kWarpMma = 1, kWarpEpi = 4, kWarpSearch = kWarpEpi + kNumEpiWarps, kNumSearchWarps = 4;
+constexpr int kThreads = 32 * (kWarpSearch + kNumSearchWarps);  // 768
+// Registers per thread: launched at kRegLaunch, then moved between groups with setmaxnreg so the
+// epilogue gets kRegEpi. The shares must add up to the launch total exactly (an increase waits
+// until decreases have freed enough), per sub-partition as well as per CTA.
+constexpr int kRegLaunch = 80, kRegCtl = 40, kRegEpi = 96, kRegSearch = 56;
+static_assert(kRegCtl + 4 * kRegEpi + kRegSearch == 6 * kRegLaunch, "register split must match the launch total");
+static_assert(kThreads * kRegLaunch <= 65536, "register file");
 constexpr uint64_t kTimeoutNs = 2000000000ull;
-constexpr int kSmemTuples = 64;
 constexpr uint32_t kXCol = 256;
+constexpr int kL0K = 64;     // layer-0 contraction width (48 used, zero padded to one 128-byte row)
+constexpr int kL0Kused = 48;
+// Column group whose warps combine the partial argmax: its layer-0 units (3 and 7) are the last
+// ones the next tile's first MMAs need.
+constexpr int kArgG = 3;
 
-constexpr int kOffY = 0;
-constexpr int kYBytes = kM * kHid * 2;
-constexpr int kOffStage = kOffY + kYBytes;
-constexpr int kOffW0 = kOffStage + kStages * kStageBytes;
-constexpr int kOffB0 = kOffW0 + 7 * kHid * 4;
-constexpr int kOffTup = kOffB0 + kHid * 4;
-constexpr int kOffOrd = kOffTup + kSmemTuples * 32;
-constexpr int kOffTidx = kOffOrd + kSmemTuples * 2;
-constexpr int kOffBar = kOffTidx + 2 * kM * 4;
-constexpr int kNumBars = 2 * kStages + 1 + 1 + 8 + 2 + 2 + 1;
-constexpr int kOffMisc = kOffBar + kNumBars * 8;
-constexpr int kSmemBytes = kOffMisc + 16 + 1024;
+// Shared memory: u (the FC1 output as swizzled K-blocks of 128 rows x 128 bytes; its first 16 KB
+// also hold the next tile's layer-0 operand between the last FC2 and the next FC1 epilogue), the
+// weight stages, the predicted-tuple handoff to the search warps, the barriers, the partial argmax.
+template <bool F8>
+struct Layout {
+    static constexpr int kStages = F8 ? 4 : 3;
+    static constexpr int kYBytes = kM * kHid * (F8 ? 1 : 2);
+    static constexpr int kOffStage = kYBytes;
+    static constexpr int kOffTidx = kOffStage + kStages * kStageBytes;
+    static constexpr int kOffBar = kOffTidx + 2 * kM * 4;
+    static constexpr int kNumBars = 2 * kStages + 1 + 1 + 8 + 2 + 2 + 1 + 1 + 1;
+    static constexpr int kOffMisc = kOffBar + kNumBars * 8;
+    // per-row partial argmax of the four column groups ([4][128] floats, then [4][128] ints): in
+    // the u buffer's second half for BF16 (idle from the last FC2 to the next tile's FC1 chunk 1),
+    // in a region of its own for FP8
+    static constexpr int kOffPart = F8 ? kOffMisc + 16 : 65536;
+    static constexpr int kSmemBytes = (F8 ? kOffPart + 4096 : kOffMisc + 16) + 1024;  // + slack to align the base
+    static_assert(kSmemBytes <= 232448, "exceeds the 227 KB of shared memory per CTA");
+};
 }  // namespace tc256
 
-// 20 warps: at most 5 per SM sub-partition, whose 16K-entry register file then holds 96 registers
-// per thread (5 x 32 x 96 = 15,360).
+// 24 warps, launched at 80 registers per thread (6 x 32 x 80 = 15,360 of a sub-partition's 16K);
+// after setup the control group drops to 40, the search group to 56 and the epilogue rises to 96.
 template <bool F8>
-__global__ void __maxnreg__(96)
+__global__ void __launch_bounds__(tc256::kThreads, 1)
     k_tc256_classify(const __grid_constant__ CUtensorMap tm_hid, const __grid_constant__ CUtensorMap tm_out,
-                     const TcParams p) {
+                     const __grid_constant__ CUtensorMap tm_l0, const TcParams p) {
     using namespace tc256;
+    using Lay = Layout<F8>;
+    constexpr int kStages = Lay::kStages;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint8_t *sY = smem + kOffY;
-    uint8_t *sStage = smem + kOffStage;
-    float *sW0 = reinterpret_cast<float *>(smem + kOffW0);
-    float *sB0 = reinterpret_cast<float *>(smem + kOffB0);
-    TupleDesc *sTup = reinterpret_cast<TupleDesc *>(smem + kOffTup);
-    uint16_t *sOrd = reinterpret_cast<uint16_t *>(smem + kOffOrd);
-    int32_t *sTidx = reinterpret_cast<int32_t *>(smem + kOffTidx);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kOffBar);
+    uint8_t *sY = smem;
+    uint8_t *sStage = smem + Lay::kOffStage;
+    int32_t *sTidx = reinterpret_cast<int32_t *>(smem + Lay::kOffTidx);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + Lay::kOffBar);
     uint64_t *full = bars, *empty = bars + kStages;
     uint64_t *acc_full = bars + 2 * kStages, *acc_empty = acc_full + 1;
     uint64_t *act = acc_empty + 1;  // 8 barriers, one per K-block of the next layer's input
-    uint64_t *tfull = act + 8, *tempty = tfull + 2, *drain = tempty + 2;
-    uint32_t *sTmem = reinterpret_cast<uint32_t *>(smem + kOffMisc);
-    volatile int *sAbort = reinterpret_cast<volatile int *>(smem + kOffMisc + 4);
+    uint64_t *tfull = act + 8, *tempty = tfull + 2, *drain = tempty + 2, *part_full = drain + 1;
+    uint64_t *feat_full = part_full + 1;  // the layer-0 operand of the current tile is in place
+    float *sPartBest = reinterpret_cast<float *>(smem + Lay::kOffPart);
+    int32_t *sPartArg = reinterpret_cast<int32_t *>(smem + Lay::kOffPart + 2048);
+    uint32_t *sTmem = reinterpret_cast<uint32_t *>(smem + Lay::kOffMisc);
+    volatile int *sAbort = reinterpret_cast<volatile int *>(smem + Lay::kOffMisc + 4);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     constexpr int KB = F8 ? 4 : 8;
@@ -94,22 +128,16 @@ __global__ void __maxnreg__(96)
         }
         for (int k = 0; k < 8; ++k) ptx::mbar_init(&act[k], kActArrivals);
         ptx::mbar_init(drain, 1);
+        ptx::mbar_init(part_full, 4 * (kNumEpiWarps / 4 - 1));
+        ptx::mbar_init(feat_full, 4);
         *sAbort = 0;
         ptx::fence_mbar_init();
     }
     if (warp == kWarpProd && lane == 0) {
         ptx::prefetch_tmap(&tm_hid);
         ptx::prefetch_tmap(&tm_out);
+        ptx::prefetch_tmap(&tm_l0);
     }
-    for (int i = threadIdx.x; i < 7 * kHid; i += kThreads) sW0[i] = p.W0[i];
-    for (int i = threadIdx.x; i < kHid; i += kThreads) sB0[i] = p.b0[i];
-    const Tables tb = *p.tables;
-    const bool tup_smem = tb.T <= uint32_t(kSmemTuples);
-    if (tup_smem)
-        for (uint32_t i = threadIdx.x; i < tb.T; i += kThreads) {
-            sTup[i] = tb.tuples[i];
-            sOrd[i] = tb.order[i];
-        }
     if (warp == kWarpMma) {
         ptx::tmem_alloc(sTmem, 512);
         ptx::tmem_relinquish();
@@ -118,29 +146,50 @@ __global__ void __maxnreg__(96)
     __syncthreads();
     ptx::tc_fence_after();
     const uint32_t tmem = *sTmem;
-
     auto fail = [&](int code) {
         atomicOr(p.err, code);
         *sAbort = 1;
     };
 
+    // Each warp group enters its branch whole and first moves its register share (setmaxnreg
+    // is executed by all warps of the group at the same point).
+    if (warp < kWarpEpi) {
+        asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kRegCtl));
     if (warp == kWarpProd) {
         if (lane == 0) {
             uint32_t stage = 0, phase = 0, n_loads = 0;
             bool ok = true;
+            auto next_stage = [&]() -> uint8_t * {
+                if (!ptx::mbar_wait(&empty[stage], phase ^ 1, sAbort, kTimeoutNs)) {
+                    fail(1);
+                    ok = false;
+                    return nullptr;
+                }
+                TC_TRACE(trace::kProd + n_loads, n_loads < trace::kLoads);
+                ++n_loads;
+                return sStage + stage * kStageBytes;
+            };
+            auto advance = [&]() {
+                if (++stage == kStages) {
+                    stage = 0;
+                    phase ^= 1;
+                }
+            };
             for (uint32_t tile = blockIdx.x; tile < p.n_tiles && ok; tile += gridDim.x) {
+                // layer 0: two 256-row chunks of the [512][64] BF16 operand, one stage each
+                for (int c = 0; c < 2 && ok; ++c) {
+                    uint8_t *dst = next_stage();
+                    if (!dst) break;
+                    ptx::mbar_arrive_expect_tx(&full[stage], kStageBytes);
+                    ptx::tma_load_2d(dst, &tm_l0, &full[stage], 0, c * 256);
+                    advance();
+                }
                 for (int L = 0; L <= kLayers && ok; ++L) {
                     const int nch = L == kLayers ? 1 : 2;
                     for (int c = 0; c < nch && ok; ++c)
                         for (int kb = 0; kb < KB; ++kb) {
-                            if (!ptx::mbar_wait(&empty[stage], phase ^ 1, sAbort, kTimeoutNs)) {
-                                fail(1);
-                                ok = false;
-                                break;
-                            }
-                            TC_TRACE(trace::kProd + n_loads, n_loads < trace::kLoads);
-                            ++n_loads;
-                            uint8_t *dst = sStage + stage * kStageBytes;
+                            uint8_t *dst = next_stage();
+                            if (!dst) break;
                             if (L < kLayers) {
                                 ptx::mbar_arrive_expect_tx(&full[stage], kStageBytes);
                                 ptx::tma_load_2d(dst, &tm_hid, &full[stage], kb * KBW, L * kHid + c * 256);
@@ -148,13 +197,11 @@ __global__ void __maxnreg__(96)
                                 ptx::mbar_arrive_expect_tx(&full[stage], p.Cpad * 128);
                                 ptx::tma_load_2d(dst, &tm_out, &full[stage], kb * KBW, 0);
                             }
-                            if (++stage == kStages) {
-                                stage = 0;
-                                phase ^= 1;
-                            }
+                            advance();
                         }
                 }
             }
+            // let the loads still in flight land before the CTA exits (bounded, abort ignored)
             volatile int never = 0;
             for (int s = 0; s < kStages; ++s) {
                 const uint32_t par = s < int(stage) ? phase : phase ^ 1;
@@ -162,49 +209,78 @@ __global__ void __maxnreg__(96)
             }
         }
     } else if (warp == kWarpMma) {
+        // One thread issues every MMA. Plain loops over register state: this warp's issue rate
+        // bounds the tensor pipe's, so it keeps no state in captured lambdas or local memory.
         if (lane == 0) {
             const uint32_t idesc_h = ptx::idesc_make(128, 256, F8);
             const uint32_t idesc_o = ptx::idesc_make(128, p.Cpad, F8);
+            const uint32_t idesc_0 = ptx::idesc_make(128, 256, false);  // layer 0: BF16 on both paths
             const uint32_t y_addr = ptx::smem_u32(sY), st_addr = ptx::smem_u32(sStage);
-            uint32_t stage = 0, phase = 0, uses = 0, lay = 0;
-            bool ok = true;
-            for (uint32_t tile = blockIdx.x; tile < p.n_tiles && ok; tile += gridDim.x) {
-                for (int L = 0; L <= kLayers && ok; ++L, ++lay) {
+            const uint64_t a0_desc = ptx::sdesc_sw128(y_addr);
+            uint32_t stage = 0, phase = 0, uses = 0, lay = 0, ntile = 0;
+            int err = 0;
+            for (uint32_t tile = blockIdx.x; tile < p.n_tiles && !err; tile += gridDim.x, ++ntile) {
+                // ---- layer 0: A = the header bytes (shared memory), B = the split weights
+                for (int c = 0; c < 2; ++c, ++uses) {
+                    TC_TRACE(trace::kMma + uses * 12 + 0, uses < uint32_t(trace::kChunks));
+                    if (uses > 0 && !ptx::mbar_wait(acc_empty, (uses - 1) & 1, sAbort, kTimeoutNs)) {
+                        err = 2;
+                        break;
+                    }
+                    TC_TRACE(trace::kMma + uses * 12 + 1, uses < uint32_t(trace::kChunks));
+                    if (c == 0 && !ptx::mbar_wait(feat_full, ntile & 1, sAbort, kTimeoutNs)) {
+                        err = 512;
+                        break;
+                    }
+                    if (!ptx::mbar_wait(&full[stage], phase, sAbort, kTimeoutNs)) {
+                        err = 8;
+                        break;
+                    }
+                    TC_TRACE(trace::kMma + uses * 12 + 2, uses < uint32_t(trace::kChunks));
+                    ptx::tc_fence_after();
+                    const uint64_t bd = ptx::sdesc_sw128(st_addr + stage * kStageBytes);
+#pragma unroll
+                    for (int kk = 0; kk < kL0Kused / 16; ++kk) ptx::mma_ss(tmem, a0_desc + 2 * kk, bd + 2 * kk, idesc_0, kk != 0, false);
+                    ptx::mma_commit(&empty[stage]);
+                    if (++stage == kStages) {
+                        stage = 0;
+                        phase ^= 1;
+                    }
+                    ptx::mma_commit(acc_full);
+                    TC_TRACE(trace::kMma + uses * 12 + 10, uses < uint32_t(trace::kChunks));
+                }
+                for (int L = 0; L <= kLayers && !err; ++L, ++lay) {
                     const bool a_tmem = (L & 1) == 0;  // FC1 and the output layer read x from TMEM
                     const int nch = L == kLayers ? 1 : 2;
                     const uint32_t idesc = L == kLayers ? idesc_o : idesc_h;
-                    for (int c = 0; c < nch && ok; ++c, ++uses) {
-                        const bool tr = uses < uint32_t(trace::kChunks);
-                        TC_TRACE(trace::kMma + uses * 12 + 0, tr);
-                        if (uses > 0 && !ptx::mbar_wait(acc_empty, (uses - 1) & 1, sAbort, kTimeoutNs)) {
-                            fail(2);
-                            ok = false;
+                    for (int c = 0; c < nch && !err; ++c, ++uses) {
+                        TC_TRACE(trace::kMma + uses * 12 + 0, uses < uint32_t(trace::kChunks));
+                        if (!ptx::mbar_wait(acc_empty, (uses - 1) & 1, sAbort, kTimeoutNs)) {
+                            err = 2;
                             break;
                         }
-                        TC_TRACE(trace::kMma + uses * 12 + 1, tr);
+                        TC_TRACE(trace::kMma + uses * 12 + 1, uses < uint32_t(trace::kChunks));
                         ptx::tc_fence_after();
                         for (int kb = 0; kb < KB; ++kb) {
                             if (c == 0 && !ptx::mbar_wait(&act[kb], lay & 1, sAbort, kTimeoutNs)) {
-                                fail(4);
-                                ok = false;
+                                err = 4;
                                 break;
                             }
                             if (!ptx::mbar_wait(&full[stage], phase, sAbort, kTimeoutNs)) {
-                                fail(8);
-                                ok = false;
+                                err = 8;
                                 break;
                             }
-                            TC_TRACE(trace::kMma + uses * 12 + 2 + kb, tr);
+                            TC_TRACE(trace::kMma + uses * 12 + 2 + kb, uses < uint32_t(trace::kChunks));
                             ptx::tc_fence_after();
-                            const uint32_t b_base = st_addr + stage * kStageBytes;
+                            const uint64_t bd = ptx::sdesc_sw128(st_addr + stage * kStageBytes);
+                            if (a_tmem) {
+                                const uint32_t ta = tmem + kXCol + kb * 32;
 #pragma unroll
-                            for (int kk = 0; kk < 4; ++kk) {
-                                const uint64_t bd = ptx::sdesc_sw128(b_base + kk * 32);
-                                const uint32_t accum = (kb | kk) != 0;
-                                if (a_tmem)
-                                    ptx::mma_ts(tmem, tmem + kXCol + kb * 32 + kk * 8, bd, idesc, accum, F8);
-                                else
-                                    ptx::mma_ss(tmem, ptx::sdesc_sw128(y_addr + kb * 16384 + kk * 32), bd, idesc, accum, F8);
+                                for (int kk = 0; kk < 4; ++kk) ptx::mma_ts(tmem, ta + kk * 8, bd + 2 * kk, idesc, (kb | kk) != 0, F8);
+                            } else {
+                                const uint64_t ad = a0_desc + uint64_t(kb) * (16384 >> 4);
+#pragma unroll
+                                for (int kk = 0; kk < 4; ++kk) ptx::mma_ss(tmem, ad + 2 * kk, bd + 2 * kk, idesc, (kb | kk) != 0, F8);
                             }
                             ptx::mma_commit(&empty[stage]);
                             if (++stage == kStages) {
@@ -212,17 +288,20 @@ __global__ void __maxnreg__(96)
                                 phase ^= 1;
                             }
                         }
-                        if (!ok) break;
+                        if (err) break;
                         ptx::mma_commit(acc_full);
-                        TC_TRACE(trace::kMma + uses * 12 + 10, tr);
+                        TC_TRACE(trace::kMma + uses * 12 + 10, uses < uint32_t(trace::kChunks));
                     }
                 }
             }
+            if (err) fail(err);
             volatile int never = 0;
             ptx::mma_commit(drain);
             ptx::mbar_wait(drain, 0, &never, kTimeoutNs);
         }
+    }  // warps 2 and 3 of the control group have no role
     } else if (warp < kWarpSearch) {
+        asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kRegEpi));
         // ---------------- 16 epilogue warps ----------------
         const int ew = warp - kWarpEpi;
         const int q = warp & 3;   // TMEM lane quadrant
@@ -255,14 +334,13 @@ __global__ void __maxnreg__(96)
             __syncwarp();
             if (lane == 0) ptx::mbar_arrive(&act[col0 / KBW]);
         };
-        // ReLU, quantise and store 32 activations (columns col0 ..) of the next layer's input
-        auto emit = [&](float *v, int col0, bool to_x, float s_out) {
-#pragma unroll
-            for (int j = 0; j < 32; ++j) v[j] = fmaxf(v[j], 0.f);
+        // ReLU, round and store 32 activations (columns col0 ..) of the next layer's input; for FP8
+        // the values are already in the next layer's scaled units
+        auto emit = [&](const float *v, int col0, bool to_x) {
             if (!F8) {
                 uint32_t w[16];
 #pragma unroll
-                for (int j = 0; j < 16; ++j) w[j] = pack_bf16(v[2 * j], v[2 * j + 1]);
+                for (int j = 0; j < 16; ++j) w[j] = relu_bf16x2(v[2 * j], v[2 * j + 1]);
                 if (to_x)
                     ptx::tmem_st16(x_col(col0), w);
                 else
@@ -271,57 +349,94 @@ __global__ void __maxnreg__(96)
                 uint32_t w[8];
 #pragma unroll
                 for (int j = 0; j < 8; ++j)
-                    w[j] = pack_e4m3x4(v[4 * j] * s_out, v[4 * j + 1] * s_out, v[4 * j + 2] * s_out, v[4 * j + 3] * s_out);
+                    w[j] = relu_e4m3x2(v[4 * j], v[4 * j + 1]) | (relu_e4m3x2(v[4 * j + 2], v[4 * j + 3]) << 16);
                 if (to_x)
                     ptx::tmem_st8(x_col(col0), w);
                 else
                     store_smem(w, col0);
             }
         };
+        // Layer-0 operand of tile t, row r (the g == 0 warps): the header bytes as BF16 in the
+        // swizzled K-major layout the MMA reads, [hi(7), lo(7)] three times, then 1, 1, 1, zeros.
+        auto write_features = [&](uint32_t t) {
+            const uint32_t it = t * kM + r;
+            const uint4 hv = it < p.n ? __ldcs(reinterpret_cast<const uint4 *>(p.headers + it)) : make_uint4(0, 0, 0, 0);
+            const uint32_t f[7] = {hv.x >> 16, hv.x & 0xFFFFu, hv.y >> 16, hv.y & 0xFFFFu, hv.z & 0xFFFFu, hv.z >> 16,
+                                   hv.w & 0xFFu};
+            float e[14];
+#pragma unroll
+            for (int k = 0; k < 7; ++k) {
+                e[k] = float(f[k] >> 8);
+                e[7 + k] = float(f[k] & 0xFFu);
+            }
+            uint32_t part[7];  // the 14 byte values as 7 BF16 pairs
+#pragma unroll
+            for (int k = 0; k < 7; ++k) part[k] = pack_bf16(e[2 * k], e[2 * k + 1]);
+            uint32_t w[32];
+#pragma unroll
+            for (int rep = 0; rep < 3; ++rep)
+#pragma unroll
+                for (int k = 0; k < 7; ++k) w[7 * rep + k] = part[k];
+            w[21] = pack_bf16(1.f, 1.f);
+            w[22] = pack_bf16(1.f, 0.f);
+#pragma unroll
+            for (int k = 23; k < 32; ++k) w[k] = 0u;
+            uint8_t *row = sY + r * 128;
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                *reinterpret_cast<uint4 *>(row + ((j ^ (r & 7)) << 4)) = make_uint4(w[4 * j], w[4 * j + 1], w[4 * j + 2], w[4 * j + 3]);
+            ptx::fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) ptx::mbar_arrive(feat_full);
+        };
 
+        if (g == 0) write_features(blockIdx.x);
         for (uint32_t tile = blockIdx.x; tile < p.n_tiles && ok; tile += gridDim.x) {
             const uint32_t i = tile * kM + r;
-            float f[7];
-            {
-                uint4 v = i < p.n ? __ldg(reinterpret_cast<const uint4 *>(p.headers + i)) : make_uint4(0, 0, 0, 0);
-                f[0] = float(v.x >> 16);
-                f[1] = float(v.x & 0xFFFFu);
-                f[2] = float(v.y >> 16);
-                f[3] = float(v.y & 0xFFFFu);
-                f[4] = float(v.z & 0xFFFFu);
-                f[5] = float(v.z >> 16);
-                f[6] = float(v.w & 0xFFu);
-            }
-            // ---- layer 0 (FP32, CUDA cores): units g and g+4 of x
-            for (int h = 0; h < 2; ++h) {
-                const int unit = g + 4 * h;
-#pragma unroll
-                for (int s = 0; s < 2; ++s) {
-                    const int col0 = unit * 64 + s * 32;
-                    float v[32];
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        float a = sB0[col0 + j];
-#pragma unroll
-                        for (int t = 0; t < 7; ++t) a = fmaf(f[t], sW0[t * kHid + col0 + j], a);
-                        v[j] = a;
-                    }
-                    emit(v, col0, true, F8 ? sa[0] : 1.f);
+            // ---- layer 0 from the accumulator (bias included): units 4c+g of x
+            for (int c = 0; c < 2; ++c, ++uses) {
+                if (!ptx::mbar_wait(acc_full, uses & 1, sAbort, kTimeoutNs)) {
+                    fail(16);
+                    ok = false;
+                    break;
                 }
+                ptx::tc_fence_after();
+                const int unit = 4 * c + g;
+                uint32_t a0[32], a1[32];
+                ptx::tmem_ld32(tmem + lane_base + g * 64, a0);
+                ptx::tmem_ld32(tmem + lane_base + g * 64 + 32, a1);
+                ptx::tmem_wait_ld();
+                ptx::tc_fence_before();
+                __syncwarp();
+                if (lane == 0) ptx::mbar_arrive(acc_empty);
+                emit(reinterpret_cast<const float *>(a0), unit * 64, true);
+                emit(reinterpret_cast<const float *>(a1), unit * 64 + 32, true);
                 ptx::tmem_wait_st();
                 act_arrive(unit * 64);
             }
+            if (!ok) break;
             // ---- hidden layers, two 256-column chunks each
             for (int L = 0; L < kLayers && ok; ++L) {
                 const bool fc2 = (L & 1) != 0;
-                const float *bias = p.bias + L * kHid;
-                const float *dq = F8 ? p.dq + L * kHid : nullptr;
-                const float s_out = F8 ? sa[L + 1] : 1.f;
-                const float s_res = F8 ? 1.f / sa[fc2 ? L - 1 : L] : 1.f;
+                // BF16: v = acc + b. FP8: v = acc * (dq * s_out) + b * s_out, in the output's units.
+                const float4 *bv = reinterpret_cast<const float4 *>(F8 ? p.fold8 + size_t(kLayers + L) * kHid
+                                                                        : p.bias + size_t(L) * kHid);
+                const float4 *dv = F8 ? reinterpret_cast<const float4 *>(p.fold8 + size_t(L) * kHid) : nullptr;
+                // FP8 residual: x is stored in the units of its own layer input (scale s[L-1])
+                const float rr = F8 && fc2 ? sa[L + 1] / sa[L - 1] : 1.f;
                 for (int c = 0; c < 2; ++c, ++uses) {
-                    const bool tr = lane == 0 && q == 2 && g < 2 && uses < uint32_t(trace::kChunks);
-                    const int tslot = trace::kEpi + (g * trace::kChunks + int(uses)) * 4;
+                    [[maybe_unused]] const bool tr = lane == 0 && q == 2 && g < 2 && uses < uint32_t(trace::kChunks);
+                    [[maybe_unused]] const int tslot = trace::kEpi + (g * trace::kChunks + int(uses)) * 4;
                     TC_TRACE(tslot + 0, tr);
+                    // the next chunk's bias (and FP8 scale) lines of this warp's unit into L1
+                    {
+                        const int nL = c == 0 ? L : L + 1, nunit = 4 * (c ^ 1) + g;
+                        if (nL < kLayers && lane < (F8 ? 4 : 2)) {
+                            const float *src = F8 ? p.fold8 + size_t((lane & 2 ? kLayers : 0) + nL) * kHid + nunit * 64 + (lane & 1) * 32
+                                                  : p.bias + size_t(nL) * kHid + nunit * 64 + lane * 32;
+                            asm volatile("prefetch.global.L1 [%0];" ::"l"(src));
+                        }
+                    }
                     if (!ptx::mbar_wait(acc_full, uses & 1, sAbort, kTimeoutNs)) {
                         fail(16);
                         ok = false;
@@ -345,9 +460,22 @@ __global__ void __maxnreg__(96)
                         const uint32_t *a = s == 0 ? a0 : a1;
                         float v[32];
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) {
-                            const float y = __uint_as_float(a[j]);
-                            v[j] = F8 ? fmaf(y, __ldg(dq + col0 + j), __ldg(bias + col0 + j)) : y + __ldg(bias + col0 + j);
+                        for (int j4 = 0; j4 < 8; ++j4) {
+                            const float4 b = __ldg(bv + col0 / 4 + j4);
+                            const float y0 = __uint_as_float(a[4 * j4]), y1 = __uint_as_float(a[4 * j4 + 1]);
+                            const float y2 = __uint_as_float(a[4 * j4 + 2]), y3 = __uint_as_float(a[4 * j4 + 3]);
+                            if (F8) {
+                                const float4 d = __ldg(dv + col0 / 4 + j4);
+                                v[4 * j4 + 0] = fmaf(y0, d.x, b.x);
+                                v[4 * j4 + 1] = fmaf(y1, d.y, b.y);
+                                v[4 * j4 + 2] = fmaf(y2, d.z, b.z);
+                                v[4 * j4 + 3] = fmaf(y3, d.w, b.w);
+                            } else {
+                                v[4 * j4 + 0] = y0 + b.x;
+                                v[4 * j4 + 1] = y1 + b.y;
+                                v[4 * j4 + 2] = y2 + b.z;
+                                v[4 * j4 + 3] = y3 + b.w;
+                            }
                         }
                         if (fc2) {
                             if (!F8) {
@@ -364,12 +492,16 @@ __global__ void __maxnreg__(96)
                                 ptx::tmem_ld8(x_col(col0), xr);
                                 ptx::tmem_wait_ld();
 #pragma unroll
-                                for (int j = 0; j < 8; ++j)
-#pragma unroll
-                                    for (int b = 0; b < 4; ++b) v[4 * j + b] += e4m3_to_f((xr[j] >> (8 * b)) & 0xFFu) * s_res;
+                                for (int j = 0; j < 8; ++j) {
+                                    const float2 lo = e4m3x2_to_f2(xr[j]), hi = e4m3x2_to_f2(xr[j] >> 16);
+                                    v[4 * j + 0] = fmaf(lo.x, rr, v[4 * j + 0]);
+                                    v[4 * j + 1] = fmaf(lo.y, rr, v[4 * j + 1]);
+                                    v[4 * j + 2] = fmaf(hi.x, rr, v[4 * j + 2]);
+                                    v[4 * j + 3] = fmaf(hi.y, rr, v[4 * j + 3]);
+                                }
                             }
                         }
-                        emit(v, col0, fc2, s_out);
+                        emit(v, col0, fc2);
                     }
                     if (fc2)
                         ptx::tmem_wait_st();
@@ -377,10 +509,14 @@ __global__ void __maxnreg__(96)
                         ptx::fence_proxy_async_smem();
                     act_arrive(unit * 64);
                     TC_TRACE(tslot + 3, tr);
+                    // after the last FC2 chunk (its MMAs, the last readers of u, have completed):
+                    // the next tile's layer-0 operand
+                    if (L == kLayers - 1 && c == 1 && g == 0 && tile + gridDim.x < p.n_tiles) write_features(tile + gridDim.x);
                 }
             }
             if (!ok) break;
-            // ---- output layer: logits and argmax on the g == 0 warps
+            // ---- output layer: each column group takes a quarter of the logits; the kArgG
+            // warps combine the four partial maxima per row and hand the prediction on
             {
                 if (!ptx::mbar_wait(acc_full, uses & 1, sAbort, kTimeoutNs)) {
                     fail(32);
@@ -389,23 +525,24 @@ __global__ void __maxnreg__(96)
                 }
                 ++uses;
                 ptx::tc_fence_after();
+                float best = -INFINITY;
                 int arg = 0;
-                if (g == 0) {
-                    float best = -INFINITY;
+                {
+                    const uint32_t cq = p.Cpad / 4;  // a multiple of 8
                     const float *bias = p.bias + kLayers * kHid;
                     const float *dq = F8 ? p.dq + kLayers * kHid : nullptr;
-                    for (uint32_t c0 = 0; c0 < p.Cpad; c0 += 32) {
-                        uint32_t a[32];
-                        ptx::tmem_ld32(tmem + lane_base + c0, a);
+                    for (uint32_t c0 = uint32_t(g) * cq; c0 < uint32_t(g + 1) * cq; c0 += 8) {
+                        uint32_t a[8];
+                        ptx::tmem_ld8(tmem + lane_base + c0, a);
                         ptx::tmem_wait_ld();
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) {
+                        for (int j = 0; j < 8; ++j) {
                             const uint32_t cc = c0 + j;
                             if (cc >= p.C) break;
                             float z = __uint_as_float(a[j]);
                             z = F8 ? fmaf(z, __ldg(dq + cc), __ldg(bias + cc)) : z + __ldg(bias + cc);
                             if (p.logits && i < p.n) p.logits[size_t(i) * p.C + cc] = z;
-                            if (z > best) {
+                            if (z > best) {  // first index of the maximum, as a serial scan
                                 best = z;
                                 arg = int(cc);
                             }
@@ -415,17 +552,39 @@ __global__ void __maxnreg__(96)
                 ptx::tc_fence_before();
                 __syncwarp();
                 if (lane == 0) ptx::mbar_arrive(acc_empty);
-                if (g == 0) {
-                    if (p.tuple && i < p.n) p.tuple[i] = arg;
+                const uint32_t t = tcnt & 1, tu = tcnt >> 1;  // this CTA's tile count: barrier parities
+                ++tcnt;
+                if (g != kArgG) {
+                    sPartBest[g * kM + r] = best;
+                    sPartArg[g * kM + r] = arg;
+                    __syncwarp();
+                    if (lane == 0) ptx::mbar_arrive(part_full);
+                } else {
+                    if (!ptx::mbar_wait(part_full, t, sAbort, kTimeoutNs)) {
+                        fail(256);
+                        ok = false;
+                        break;
+                    }
+                    // groups in column order, strict > keeps the lowest column among equal maxima
+                    float b = sPartBest[r];
+                    int am = sPartArg[r];
+#pragma unroll
+                    for (int gg = 1; gg < 4; ++gg) {
+                        const float bg = gg == kArgG ? best : sPartBest[gg * kM + r];
+                        const int ag = gg == kArgG ? arg : sPartArg[gg * kM + r];
+                        if (bg > b) {
+                            b = bg;
+                            am = ag;
+                        }
+                    }
+                    if (p.tuple && i < p.n) p.tuple[i] = am;
                     if (p.fused_search) {
-                        const uint32_t t = tcnt & 1, tu = tcnt >> 1;
-                        ++tcnt;
                         if (!ptx::mbar_wait(&tempty[t], (tu & 1) ^ 1, sAbort, kTimeoutNs)) {
                             fail(64);
                             ok = false;
                             break;
                         }
-                        sTidx[t * kM + r] = arg;
+                        sTidx[t * kM + r] = am;
                         __syncwarp();
                         if (lane == 0) ptx::mbar_arrive(&tfull[t]);
                     }
@@ -433,11 +592,11 @@ __global__ void __maxnreg__(96)
             }
         }
     } else {
+        asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kRegSearch));
         // ---------------- search warps ----------------
         if (p.fused_search) {
+            const Tables tb = *p.tables;
             const int r = (warp - kWarpSearch) * 32 + lane;
-            const TupleDesc *tuples = tup_smem ? sTup : tb.tuples;
-            const uint16_t *order = tup_smem ? sOrd : tb.order;
             uint32_t tcnt = 0;
             uint32_t st_pk = 0, st_match = 0, st_correct = 0, st_hit = 0, st_fb = 0;
             Counters cn{0, 0, 0};
@@ -448,28 +607,29 @@ __global__ void __maxnreg__(96)
                     fail(128);
                     break;
                 }
-                // each search thread owns rows r and r + 64 of the tile
-                const int pred0 = sTidx[t * kM + r], pred1 = sTidx[t * kM + r + 64];
+                [[maybe_unused]] const bool trs = r == 0 && tcnt <= uint32_t(trace::kSearchTiles);
+                TC_TRACE(trace::kSearch + 2 * (tcnt - 1), trs);
+                // each search thread owns row r of the tile
+                const int pred = sTidx[t * kM + r];
                 __syncwarp();
                 if (lane == 0) ptx::mbar_arrive(&tempty[t]);
-                for (int h2 = 0; h2 < 2; ++h2) {
-                    const uint32_t i = tile * kM + r + 64 * h2;
-                    const int pred = h2 ? pred1 : pred0;
-                    if (i < p.n) {
-                        const Hdr h = load_header(p.headers + i);
-                        Best best;
-                        const bool hit = search_packet(tb, tuples, order, h, pred, best, cn);
-                        p.ids[i] = best.id;
-                        if (p.stats) {
-                            st_pk++;
-                            const bool m = best.id != 0xFFFFFFFFu;
-                            st_match += m;
-                            st_correct += m && int(best.tuple) == pred;
-                            st_hit += hit;
-                            st_fb += !hit;
-                        }
+                const uint32_t i = tile * kM + r;
+                if (i < p.n) {
+                    // headers and ids stream through L2 with evict-first hints, the tables stay
+                    const Hdr h = load_header_stream(p.headers + i);
+                    Best best;
+                    const bool hit = search_packet(tb, tb.tuples, tb.order, h, pred, best, cn);
+                    __stcs(p.ids + i, best.id);
+                    if (p.stats) {
+                        st_pk++;
+                        const bool m = best.id != 0xFFFFFFFFu;
+                        st_match += m;
+                        st_correct += m && int(best.tuple) == pred;
+                        st_hit += hit;
+                        st_fb += !hit;
                     }
                 }
+                TC_TRACE(trace::kSearch + 2 * (tcnt - 1) + 1, trs);
             }
             if (p.stats) {
                 auto add = [&](unsigned long long *dst, uint32_t v) {
@@ -494,35 +654,95 @@ __global__ void __maxnreg__(96)
     if (warp == kWarpMma) ptx::tmem_dealloc(tmem, 512);
 }
 
-// 256-row hidden-layer maps (the output-layer map of the 1-SM kernel is reused).
+namespace {
+struct Tc256Maps {
+    CUtensorMap hid, out, l0;
+};
+
+// Round to the nearest BF16 value, as a float.
+float bf16_round_host(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+
+// The layer-0 operand B[n][k] (n < 512, k < 64) with sum_k A[k] B[n][k] = s * (b0[n] + sum_t
+// f_t W0[t][n]) for A = [hi(7), lo(7)] x 3, 1 x 3, 0 x 19 (f_t = 256 hi_t + lo_t): the weight
+// parts scaled by 256 meet the high bytes, the plain parts the low bytes.
+void layer0_operand(const float *W0, const float *b0, float s, __nv_bfloat16 *B) {
+    auto split = [](float w, float part[3]) {
+        part[0] = bf16_round_host(w);
+        const float r1 = w - part[0];  // exact in FP32
+        part[1] = bf16_round_host(r1);
+        part[2] = bf16_round_host(r1 - part[1]);
+    };
+    for (uint32_t n = 0; n < 512; ++n) {
+        __nv_bfloat16 *row = B + size_t(n) * tc256::kL0K;
+        for (int k = 0; k < tc256::kL0K; ++k) row[k] = __float2bfloat16_rn(0.f);
+        for (int t = 0; t < 7; ++t) {
+            float part[3];
+            split(W0[size_t(t) * 512 + n] * s, part);
+            for (int pi = 0; pi < 3; ++pi) {
+                row[pi * 14 + t] = __float2bfloat16_rn(part[pi] * 256.f);
+                row[pi * 14 + 7 + t] = __float2bfloat16_rn(part[pi]);
+            }
+        }
+        float part[3];
+        split(b0[n] * s, part);
+        for (int pi = 0; pi < 3; ++pi) row[42 + pi] = __float2bfloat16_rn(part[pi]);
+    }
+}
+}  // namespace
+
+// 256-row hidden-layer maps (the output-layer map of the 1-SM kernel is reused) and the layer-0
+// operands with their maps.
 int tc256_prepare_model(tang_ctx *ctx, DeviceModel &m) {
     if (!m.d_wbf16) return TANG_OK;
-    TcMaps *maps = static_cast<TcMaps *>(aligned_alloc(64, 2 * sizeof(TcMaps)));
+    Tc256Maps *maps = static_cast<Tc256Maps *>(aligned_alloc(64, 2 * sizeof(Tc256Maps)));
     m.tmap256 = maps;
+    const float *W0 = m.host_params.data(), *b0 = W0 + size_t(7) * m.N;
+    std::vector<__nv_bfloat16> l0(size_t(2) * 512 * tc256::kL0K);
+    layer0_operand(W0, b0, 1.f, l0.data());
+    if (m.has_fp8) layer0_operand(W0, b0, m.act_scale[0], l0.data() + size_t(512) * tc256::kL0K);
+    int rc = ctx_alloc(ctx, l0.size() * 2, &m.d_l0);
+    if (rc) return rc;
+    cudaMemcpy(m.d_l0, l0.data(), l0.size() * 2, cudaMemcpyHostToDevice);
     const TcMaps *one = static_cast<const TcMaps *>(m.tmap_bf16);
     maps[0].out = one[0].out;
-    int rc = make_tmap(ctx, &maps[0].hid, m.d_wbf16, tc256::kLayers * m.N, false, 256);
-    if (rc) return rc;
+    if ((rc = make_tmap(ctx, &maps[0].hid, m.d_wbf16, tc256::kLayers * m.N, false, 256))) return rc;
+    if ((rc = make_tmap(ctx, &maps[0].l0, m.d_l0, 512, false, 256, tc256::kL0K))) return rc;
     if (m.d_wfp8) {
         const TcMaps *one8 = static_cast<const TcMaps *>(m.tmap_fp8);
         maps[1].out = one8[0].out;
-        rc = make_tmap(ctx, &maps[1].hid, m.d_wfp8, tc256::kLayers * m.N, true, 256);
+        if ((rc = make_tmap(ctx, &maps[1].hid, m.d_wfp8, tc256::kLayers * m.N, true, 256))) return rc;
+        rc = make_tmap(ctx, &maps[1].l0, static_cast<__nv_bfloat16 *>(m.d_l0) + size_t(512) * tc256::kL0K, 512, false,
+                       256, tc256::kL0K);
     }
     return rc;
 }
 
-int tc256_launch(tang_ctx *ctx, DeviceModel &m, const TcParams &prm, bool f8, cudaStream_t st, int grid_cap) {
-    if (!m.tmap256 || (f8 && !m.d_wfp8)) return TANG_EUNSUPPORTED;
-    const TcMaps &maps = static_cast<const TcMaps *>(m.tmap256)[f8 ? 1 : 0];
-    static bool attr_done[2] = {false, false};
-    if (!attr_done[f8]) {
-        cudaError_t e = f8 ? cudaFuncSetAttribute(k_tc256_classify<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                  tc256::kSmemBytes)
-                           : cudaFuncSetAttribute(k_tc256_classify<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                  tc256::kSmemBytes);
+template <bool F8>
+static int tc256_launch_t(tang_ctx *ctx, const Tc256Maps &maps, const TcParams &prm, cudaStream_t st, uint32_t grid) {
+    constexpr int kSmem = tc256::Layout<F8>::kSmemBytes;
+    static bool attr_done = false;
+    if (!attr_done) {
+        // the setmaxnreg split assumes the launch register count it was sized for: with any other
+        // count an increase could wait forever, so refuse to launch
+        cudaFuncAttributes fa{};
+        cudaError_t e = cudaFuncGetAttributes(&fa, k_tc256_classify<F8>);
+        if (e != cudaSuccess) return set_err(ctx, TANG_EDEVICE, "N=256 kernel attributes: %s", cudaGetErrorString(e));
+        if (fa.numRegs != tc256::kRegLaunch)
+            return set_err(ctx, TANG_EDEVICE, "N=256 kernel built with %d registers per thread, expected %d", fa.numRegs,
+                           tc256::kRegLaunch);
+        e = cudaFuncSetAttribute(k_tc256_classify<F8>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
         if (e != cudaSuccess) return set_err(ctx, TANG_EDEVICE, "smem attribute (N=256): %s", cudaGetErrorString(e));
-        attr_done[f8] = true;
+        attr_done = true;
     }
+    k_tc256_classify<F8><<<grid, tc256::kThreads, kSmem, st>>>(maps.hid, maps.out, maps.l0, prm);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return set_err(ctx, TANG_EDEVICE, "N=256 kernel launch: %s", cudaGetErrorString(e));
+    return TANG_OK;
+}
+
+int tc256_launch(tang_ctx *ctx, DeviceModel &m, const TcParams &prm, bool f8, cudaStream_t st, int grid_cap) {
+    if (!m.tmap256 || !m.d_l0 || (f8 && (!m.d_wfp8 || !m.d_fold8))) return TANG_EUNSUPPORTED;
+    const Tc256Maps &maps = static_cast<const Tc256Maps *>(m.tmap256)[f8 ? 1 : 0];
     uint32_t grid = uint32_t(grid_cap > 0 ? grid_cap : ctx->sm_count);
     grid = std::min<uint32_t>(prm.n_tiles, std::min<uint32_t>(grid, uint32_t(ctx->sm_count)));
     TcParams prm_t = prm;
@@ -532,12 +752,8 @@ int tc256_launch(tang_ctx *ctx, DeviceModel &m, const TcParams &prm, bool f8, cu
     cudaMemsetAsync(d_trace, 0, sizeof(unsigned long long) * trace::kTotal, st);
     prm_t.trace = d_trace;
 #endif
-    if (f8)
-        k_tc256_classify<true><<<grid, tc256::kThreads, tc256::kSmemBytes, st>>>(maps.hid, maps.out, prm_t);
-    else
-        k_tc256_classify<false><<<grid, tc256::kThreads, tc256::kSmemBytes, st>>>(maps.hid, maps.out, prm_t);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return set_err(ctx, TANG_EDEVICE, "N=256 kernel launch: %s", cudaGetErrorString(e));
+    const int rc = f8 ? tc256_launch_t<true>(ctx, maps, prm_t, st, grid) : tc256_launch_t<false>(ctx, maps, prm_t, st, grid);
+    if (rc) return rc;
 #ifdef TANG_TC_TRACE
     if (const char *path = getenv("TANG_TC_TRACE_FILE")) {
         std::vector<unsigned long long> hbuf(trace::kTotal);

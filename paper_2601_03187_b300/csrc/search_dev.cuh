@@ -24,6 +24,12 @@ __device__ __forceinline__ Hdr load_header(const tang_header *h) {
     uint4 v = __ldg(reinterpret_cast<const uint4 *>(h));
     return Hdr{v.x, v.y, v.z & 0xFFFFu, v.z >> 16, v.w & 0xFFu};
 }
+// Header read with the evict-first (streaming) cache hint: packet headers are read once or twice
+// and should not displace the hash tables from L2.
+__device__ __forceinline__ Hdr load_header_stream(const tang_header *h) {
+    uint4 v = __ldcs(reinterpret_cast<const uint4 *>(h));
+    return Hdr{v.x, v.y, v.z & 0xFFFFu, v.z >> 16, v.w & 0xFFu};
+}
 
 __device__ __forceinline__ DRule load_rule(const DRule *r) {
     uint4 a = __ldg(reinterpret_cast<const uint4 *>(r));

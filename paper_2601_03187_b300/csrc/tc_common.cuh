@@ -22,6 +22,7 @@ struct TcParams {
     const float *bias;      // [12][512] hidden biases, then [Cpad] output biases
     const float *dq;        // FP8 only: per layer and output column 1 / (act scale * weight scale)
     const float *sa;        // FP8 only: [13] activation scales of the layers' inputs
+    const float *fold8;     // FP8 only: [12][512] dq * s_out, then [12][512] bias * s_out (N=256 kernel)
     uint32_t C, Cpad;
     int fused_search;
     unsigned long long *trace;  // event timestamps of CTA 0 (trace builds only, else null)
@@ -34,7 +35,9 @@ constexpr int kMma = 0;                        // [chunk][12]: start, acc_empty 
 constexpr int kEpi = kMma + kChunks * 12;      // [warp 0/1][chunk][4]: wait, acc_full ok, drained, published
 constexpr int kProd = kEpi + 2 * kChunks * 4;  // [load]: empty ok
 constexpr int kLoads = 800;
-constexpr int kTotal = kProd + kLoads;
+constexpr int kSearch = kProd + kLoads;        // [tile][2]: search warp 0 got the tile, finished it
+constexpr int kSearchTiles = 32;
+constexpr int kTotal = kSearch + 2 * kSearchTiles;
 }  // namespace trace
 #ifdef TANG_TC_TRACE
 #define TC_TRACE(slot, limit)                                                        \
@@ -69,12 +72,32 @@ __device__ __forceinline__ float e4m3_to_f(uint32_t byte) {
     return __half2float(__half(h));
 }
 
+// ReLU, round to nearest even and pack two BF16: lo in bits 0-15, hi in bits 16-31.
+__device__ __forceinline__ uint32_t relu_bf16x2(float lo, float hi) {
+    uint32_t d;
+    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+    return d;
+}
+// ReLU, round to nearest even with saturation at +-448 and pack two E4M3 codes: lo in bits 0-7.
+__device__ __forceinline__ uint32_t relu_e4m3x2(float lo, float hi) {
+    uint16_t d;
+    asm("cvt.rn.satfinite.relu.e4m3x2.f32 %0, %1, %2;" : "=h"(d) : "f"(hi), "f"(lo));
+    return d;
+}
+// Two E4M3 codes (bits 0-7 and 8-15 of `two`) as floats; every E4M3 value is exact in FP16.
+__device__ __forceinline__ float2 e4m3x2_to_f2(uint32_t two) {
+    uint32_t h2;
+    asm("cvt.rn.f16x2.e4m3x2 %0, %1;" : "=r"(h2) : "h"(uint16_t(two & 0xFFFFu)));
+    return __half22float2(*reinterpret_cast<const __half2 *>(&h2));
+}
+
 struct TcMaps {
     CUtensorMap hid, out;
 };
 
-// Row-major [rows][512] weight matrix of 1- or 2-byte elements as a TMA tensor map whose box is
-// 128 bytes x box_rows with 128-byte swizzle.
-int make_tmap(tang_ctx *ctx, CUtensorMap *m, void *base, uint32_t rows, bool f8, uint32_t box_rows);
+// Row-major [rows][cols] weight matrix of 1- or 2-byte elements as a TMA tensor map whose box is
+// 128 bytes x box_rows with 128-byte swizzle (cols * element size a multiple of 128).
+int make_tmap(tang_ctx *ctx, CUtensorMap *m, void *base, uint32_t rows, bool f8, uint32_t box_rows,
+              uint32_t cols = 512);
 
 }  // namespace tang

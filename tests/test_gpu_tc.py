@@ -127,9 +127,15 @@ def test_predictions_agree_across_precisions(setup):
     _, t32 = infer(ctx, rs, hs, T, tg.FP32)
     _, t16 = infer(ctx, rs, hs, T, tg.BF16, "1sm")
     assert (t32 == t16).mean() > 0.9
-    # every tensor-core variant runs the same arithmetic on each row
+    # the N=128 variants run the same arithmetic on each row
     z16 = infer(ctx, rs, hs, T, tg.BF16, "1sm")[0]
-    for v in ("2sm", "mc2", "mc4", "n256"):
+    for v in ("2sm", "mc2", "mc4"):
         zv, tv = infer(ctx, rs, hs, T, tg.BF16, v)
         assert (tv == t16).all(), v
         assert (zv == z16).all(), v
+    # the N=256 kernel sums layer 0 on the tensor core (exact products, another FP32 summation
+    # order): a BF16 rounding of x may differ by one unit, so logits agree closely, not bitwise
+    zv, tv = infer(ctx, rs, hs, T, tg.BF16, "n256")
+    scale = np.abs(z16).max(axis=1, keepdims=True) + 1e-30
+    assert np.median(np.abs(zv - z16) / scale) < 1e-3
+    assert (tv == t16).mean() > 0.998
