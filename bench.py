@@ -142,9 +142,11 @@ def quick_model(ctx, rs, rules, seed):
     ctx.load_model(rs, blob)
 
 
-def measure_serving(tg, ctx, seconds=2.0):
+def measure_serving(tg, ctx, seconds=2.0, slots=8):
     """Four resident rulesets (16k, 64k, 256k, 512k), Poisson arrivals, batch sizes log-uniform in
-    [1, 65536], offered at 0.5 / 0.8 / 0.95 of the measured fused-kernel capacity."""
+    [1, 65536]. Capacity is the engine's saturated throughput on this request mix (a burst of
+    requests submitted at once, host buffers in and out); loads are offered at 0.5 / 0.8 / 0.95 of
+    it. The fused kernel's throughput on 1M-packet device batches is reported beside it."""
     import torch
     sizes = [16_384, 65_536, 262_144, 524_288]
     sets, pools = [], []
@@ -154,7 +156,7 @@ def measure_serving(tg, ctx, seconds=2.0):
         quick_model(ctx, rs, rules, 20 + k)
         sets.append(rs)
         pools.append(wl.gen_trace(rules, [("inside", 1 << 20), ("zipf", 1 << 20, 1.2)], 30 + k))
-    # capacity: fused BF16 throughput on 1M-packet batches, averaged over the rulesets
+    # kernel capacity: fused BF16 throughput on 1M-packet device batches, averaged over the rulesets
     caps = []
     for rs, pool in zip(sets, pools):
         d = torch.from_numpy(pool[: 1 << 20].view(np.uint8).reshape(-1, 16)).cuda()
@@ -166,37 +168,49 @@ def measure_serving(tg, ctx, seconds=2.0):
             ctx.classify(rs, d, ids, path="fused_bf16")
         torch.cuda.synchronize()
         caps.append(3 * (1 << 20) / (time.perf_counter() - t0) / 1e6)
-    capacity = float(np.mean(caps))
+    kernel_capacity = float(np.mean(caps))
     mean_batch = 65536 / np.log(65537)
-    ctx.serve_start(max_inflight=4, max_batch=262_144, path="fused_bf16")
-    loads = []
-    for rho in (0.5, 0.8, 0.95):
-        rate = rho * capacity * 1e6 / mean_batch
-        arr = wl.gen_serving_arrivals(int(rate * seconds) + 1, len(sets), rate, seed=int(rho * 100))
-        outs, handles, subs = [], [], []
+    ctx.serve_start(max_inflight=slots, max_batch=262_144, path="fused_bf16")
+
+    def run(arr, paced):
+        outs, handles = [], []
         t_start = time.perf_counter()
         for (t_arr, which, size, seed) in arr:
-            delay = t_start + t_arr - time.perf_counter()
-            if delay > 0:
-                time.sleep(delay)
+            if paced:
+                delay = t_start + t_arr - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
             pool = pools[which]
             off = seed % (len(pool) - size)
-            h = pool[off: off + size]
             out = np.empty(size, dtype=np.uint32)
             outs.append(out)
-            handles.append(ctx.serve_submit(sets[which], h, out))
+            handles.append(ctx.serve_submit(sets[which], pool[off: off + size], out))
         stats = [ctx.serve_poll(r, wait_ms=60000) for r in handles]
         lat = [1e3 * (s["done_s"] - s["submit_s"]) for s in stats]
         pk = sum(a[2] for a in arr)
         span = max(s["done_s"] for s in stats) - min(s["submit_s"] for s in stats)
-        loads.append({"rho": rho, "offered_mpkts": round(rho * capacity, 2), "achieved_mpkts": round(pk / span / 1e6, 2),
+        return pk / span / 1e6, lat
+
+    # saturated capacity of the engine on this mix: about `seconds` of work submitted at once
+    burst = wl.gen_serving_arrivals(int(kernel_capacity * 1e6 / mean_batch * seconds) + 1, len(sets),
+                                    kernel_capacity * 1e6 / mean_batch, seed=7)
+    run(burst[: len(burst) // 8], False)  # warm-up (graphs, staging)
+    capacity, _ = run(burst, False)
+    loads = []
+    for rho in (0.5, 0.8, 0.95):
+        rate = rho * capacity * 1e6 / mean_batch
+        arr = wl.gen_serving_arrivals(int(rate * seconds) + 1, len(sets), rate, seed=int(rho * 100))
+        achieved, lat = run(arr, True)
+        loads.append({"rho": rho, "offered_mpkts": round(rho * capacity, 2), "achieved_mpkts": round(achieved, 2),
                       "requests": len(arr), "p50_ms": round(float(np.percentile(lat, 50)), 3),
                       "p99_ms": round(float(np.percentile(lat, 99)), 3)})
     ctx.serve_stop()
     for rs in sets:
         ctx.unload_ruleset(rs)
-    return {"rulesets": sizes, "capacity_mpkts": round(capacity, 2), "batch": "log-uniform [1, 65536]",
-            "slots": 4, "max_batch": 262_144, "loads": loads}
+    return {"rulesets": sizes, "capacity_mpkts": round(capacity, 2),
+            "capacity_def": "saturated engine throughput on this request mix (host buffers in and out)",
+            "kernel_capacity_mpkts": round(kernel_capacity, 2), "batch": "log-uniform [1, 65536]",
+            "slots": slots, "max_batch": 262_144, "loads": loads}
 
 
 def measure_updates(tg, ctx, n_ops=300):
