@@ -44,6 +44,38 @@ def flops_per_packet(T):
     return 2 * 7 * HIDDEN + 2 * BLOCKS * 2 * HIDDEN * HIDDEN + 2 * HIDDEN * T
 
 
+# DRAM traffic of the fused kernel per launch, from an ncu capture summarised in profiles/. It is
+# reported only while the kernel's sources and the packet count are the ones it was taken with.
+TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "k_tc256_classify_bf16_dram_512k_16M.md")
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_2601_03187_b300", "csrc", f)
+                  for f in ("mlp_tc256.cu", "search_dev.cuh", "tc_ptx.cuh", "tc_common.cuh")]
+
+
+def kernel_digest():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def traffic_from_profile(n_packets):
+    try:
+        kv = {}
+        with open(TRAFFIC_PROFILE) as f:
+            for line in f:
+                if ":" in line and line.split(":", 1)[0].strip() in ("kernel_sources_sha256", "packets",
+                                                                       "dram_bytes_per_launch"):
+                    k, v = line.split(":", 1)
+                    kv[k.strip()] = v.strip().strip("`")
+        if kv.get("kernel_sources_sha256") != kernel_digest() or int(kv.get("packets", -1)) != n_packets:
+            return None
+        return int(kv["dram_bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -439,7 +471,7 @@ def main():
                 "ids_equal_device_path": e2e_equal},
         "gpu_launches": args.steps,
         "roofline": {"bound": "tensor", "achieved": round(achieved_tflops, 2), "peak": peak, "unit": "TFLOP/s",
-                     "frac": round(achieved_tflops / peak, 4), "traffic": None,
+                     "frac": round(achieved_tflops / peak, 4), "traffic": traffic_from_profile(n),
                      "peak_kind": "bf16 sustained (%s)" % ("of measured" if pk_src == "measured" else "of fallback"),
                      "flops_per_packet": fpp},
         "cpu_baseline": cpu,
