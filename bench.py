@@ -288,6 +288,91 @@ def measure_updates(tg, ctx, n_ops=300):
     return out
 
 
+def measure_peaks():
+    """Denominators the driver's peak file lacks, measured with library GEMMs (cuBLAS SGEMM with
+    TF32 off for FP32 SIMT; cuBLASLt E4M3 GEMM for FP8), best of a few 8192^3 runs."""
+    import torch
+    out = {}
+    def best(fn, flop, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        t = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            e1.synchronize()
+            t.append(e0.elapsed_time(e1) / 1e3)
+        return round(flop / min(t) / 1e12, 1)
+    n = 8192
+    tf32 = torch.backends.cuda.matmul.allow_tf32
+    try:
+        torch.backends.cuda.matmul.allow_tf32 = False
+        a = torch.randn(n, n, device="cuda")
+        b = torch.randn(n, n, device="cuda")
+        out["fp32_simt_tflops"] = best(lambda: a @ b, 2.0 * n ** 3)
+        del a, b
+    except Exception as e:  # noqa: BLE001
+        out["fp32_simt_error"] = str(e)[:120]
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = tf32
+    try:
+        a = torch.randn(n, n, device="cuda").to(torch.float8_e4m3fn)
+        b = torch.randn(n, n, device="cuda").to(torch.float8_e4m3fn).t()
+        one = torch.ones((), device="cuda")
+        out["fp8_tflops"] = best(lambda: torch._scaled_mm(a, b, scale_a=one, scale_b=one, out_dtype=torch.bfloat16),
+                                 2.0 * n ** 3)
+        del a, b
+    except Exception as e:  # noqa: BLE001
+        out["fp8_error"] = str(e)[:120]
+    torch.cuda.empty_cache()
+    return out
+
+
+def measure_stability(ctx, seeds=(0, 1, 2), max_packets=1 << 22):
+    """Per-packet time of the fused BF16 kernel across the configurations' rulesets and 3 rule /
+    trace seeds (quick one-epoch models; traces capped at 4M packets)."""
+    import torch
+    res = {}
+    for cfg in (0, 1, 2):
+        ns = []
+        for sd in seeds:
+            rules = wl.rules_for_config(cfg, seed=100 + sd)
+            rs = ctx.load_ruleset(rules)
+            quick_model(ctx, rs, rules, 50 + sd)
+            total = sum(part[1] for part in wl.synth.CONFIGS[cfg]["trace"])
+            tr = wl.trace_for_config(cfg, rules, scale=min(1.0, max_packets / total), seed=200 + sd)
+            d = torch.from_numpy(tr.view(np.uint8).reshape(-1, 16)).cuda()
+            ids = torch.empty(len(tr), dtype=torch.int32, device="cuda")
+            for _ in range(2):
+                ctx.classify(rs, d, ids, path="fused_bf16", graph=True)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(3):
+                ctx.classify(rs, d, ids, path="fused_bf16", graph=True)
+            e1.record()
+            e1.synchronize()
+            ns.append(e0.elapsed_time(e1) / 3 * 1e6 / len(tr))
+            ctx.unload_ruleset(rs)
+            del d, ids
+        res["config%d" % cfg] = {"ns_per_packet": [round(x, 4) for x in ns], "mean": round(float(np.mean(ns)), 4),
+                                 "std": round(float(np.std(ns)), 4), "packets": int(len(tr))}
+    return res
+
+
+def cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return None
+
+
 def run_reference(args, world, rank):
     """The oracle (plain C linear scan over rules in priority order) on this host's cores."""
     if rank != 0:
@@ -424,6 +509,38 @@ def main():
                 lat["%s_b%d" % (path, bs)] = {"p50_ms": round(float(np.percentile(ts, 50)), 4),
                                               "p99_ms": round(float(np.percentile(ts, 99)), 4)}
         extra["latency"] = lat
+        # latency per classify call from pinned host headers to host ids (H2D, kernels, D2H)
+        lat_h = {}
+        for path, iters in (("fused_bf16", 200), ("plain_fp32", 40)):
+            for bs in (8192, 65536):
+                hb = torch.empty(bs * 16, dtype=torch.uint8, pin_memory=True).numpy()
+                hb[:] = trace[:bs].view(np.uint8).reshape(-1)
+                hb = hb.view(wl.HEADER_DTYPE)
+                ob = torch.empty(bs, dtype=torch.int32, pin_memory=True).numpy().view(np.uint32)
+                for _ in range(5):
+                    ctx.classify(rs, hb, ob, path=path)
+                ts = []
+                for _ in range(iters):
+                    t0 = time.perf_counter()
+                    ctx.classify(rs, hb, ob, path=path)
+                    ts.append(1e3 * (time.perf_counter() - t0))
+                lat_h["%s_b%d" % (path, bs)] = {"p50_ms": round(float(np.percentile(ts, 50)), 4),
+                                                "p99_ms": round(float(np.percentile(ts, 99)), 4)}
+        extra["latency_host_to_host"] = lat_h
+        pk2 = measure_peaks()
+        extra["peaks_measured_here"] = pk2
+        if "fp8_tflops" in pk2:
+            a8 = extra["fused_fp8_mpkts"] * fpp / 1e6
+            extra["fp8_roofline"] = {"bound": "tensor", "achieved": round(a8, 2), "peak": pk2["fp8_tflops"],
+                                     "unit": "TFLOP/s", "frac": round(a8 / pk2["fp8_tflops"], 4),
+                                     "peak_kind": "cuBLASLt E4M3 8192^3 GEMM, burst (measured here)"}
+        if "fp32_simt_tflops" in pk2:
+            a32 = extra["plain_fp32_mpkts"] * fpp / 1e6
+            extra["plain_fp32_roofline"] = {"bound": "fp32 simt", "achieved": round(a32, 2),
+                                            "peak": pk2["fp32_simt_tflops"], "unit": "TFLOP/s",
+                                            "frac": round(a32 / pk2["fp32_simt_tflops"], 4),
+                                            "peak_kind": "cuBLAS SGEMM (TF32 off) 8192^3, burst (measured here)"}
+        extra["stability"] = measure_stability(ctx)
         extra["serving"] = measure_serving(tg, ctx)
         extra["updates"] = measure_updates(tg, ctx)
 
@@ -451,9 +568,14 @@ def main():
         t0 = time.perf_counter()
         ref = oc.classify(rules, trace[:sample], threads=cores)
         cdt = time.perf_counter() - t0
+        s1 = max(1, sample // 16)
+        t0 = time.perf_counter()
+        oc.classify(rules, trace[:s1], threads=1)
+        c1 = time.perf_counter() - t0
         cpu = {"value": round(sample / cdt / 1e6, 4), "unit": "Mpkt/s", "cores": cores, "kind": "oracle",
                "sample": "first %d packets of the 16M trace (linear scan, all cores)" % sample,
-               "ids_match_gpu": bool((ref == ids_fused[:sample]).all())}
+               "ids_match_gpu": bool((ref == ids_fused[:sample]).all()),
+               "single_thread_mpkts": round(s1 / c1 / 1e6, 5), "single_thread_sample": s1, "cpu_model": cpu_model()}
 
     if rank != 0:
         return
