@@ -288,6 +288,112 @@ def measure_updates(tg, ctx, n_ops=300):
     return out
 
 
+def measure_deferred_update(tg, ctx, n_rules=65536, windows=10, per_window=2000, tau=0.05, theta=10000,
+                            window_packets=1 << 22, train_s=4.0):
+    """The dynamic experiment of §7.3 at this library's scale. The ruleset is clustered (64 address
+    blocks, each with its own typical tuple; the headline generator's /0 prefixes make a few rules
+    match everything, and uniform addresses leave nothing to learn, so neither shows drift). Per
+    window: delete `per_window` uniform live rules and insert as many rules of "another ruleset"
+    (64 other blocks, priorities uniform over the live range) by immediate update (§5.2.1), then
+    run a window of packets drawn inside the live rules through the network (BF16) and the
+    search engine. The monitor is fed the paper-mode search's
+    memory accesses (slot + rule reads, the per-lookup cost of Tables 2-3; deterministic, where the
+    kernel's sub-millisecond time is not); the search kernel's measured throughput is reported
+    beside it. IU only vs IU + DU (tau, theta of §7.3; training capped at train_s seconds and
+    hot-swapped), from the same model and the same update sequence."""
+    import torch
+    base_rules = wl.gen_clustered_rules(n_rules, 60)
+    runs = {}
+    blob0 = None
+    for mode in ("iu_only", "iu_du"):
+        rs = ctx.load_ruleset(base_rules)
+        if blob0 is None:
+            h0 = wl.gen_trace(base_rules, [("inside", 1 << 18)], 61)
+            blob0, _ = ctx.train(rs, h0, N=HIDDEN, blocks=BLOCKS, batch=8192, epochs=1000, max_rounds=1, alpha=100,
+                                 holdout=0.05, time_budget_s=2 * train_s, seed=62)
+        ctx.load_model(rs, blob0)
+        live = {int(r["id"]): r for r in base_rules}
+        rng = np.random.default_rng(63)
+        next_id = 10 ** 7
+        rows = []
+        for w in range(windows + 1):
+            upd_s = 0.0
+            if w > 0:
+                dels = rng.choice(np.fromiter(live.keys(), dtype=np.int64), per_window, replace=False)
+                fresh = wl.gen_clustered_rules(per_window, 61, first_id=next_id, priority_range=len(live))
+                next_id += per_window
+                t0 = time.perf_counter()
+                for rid in dels:
+                    ctx.delete_rule(rs, int(rid))
+                for r in fresh:
+                    ctx.insert_rule(rs, r)
+                upd_s = time.perf_counter() - t0
+                for rid in dels:
+                    del live[int(rid)]
+                for r in fresh:
+                    live[int(r["id"])] = r
+            cur = np.array(list(live.values()), dtype=wl.RULE_DTYPE)
+            h = wl.gen_trace(cur, [("inside", window_packets)], 2000 + w)
+            d = torch.from_numpy(h.view(np.uint8).reshape(-1, 16)).cuda()
+            n = len(h)
+            pred = torch.empty(n, dtype=torch.int32, device="cuda")
+            ids = torch.empty(n, dtype=torch.int32, device="cuda")
+            ids_exact = torch.empty(n, dtype=torch.int32, device="cuda")
+            ctx.infer(rs, d, tuples=pred, precision=tg.BF16)
+            st_e = ctx.search(rs, d, pred, ids_exact, stats=True)
+            st_p = ctx.search(rs, d, pred, ids, paper=True, stats=True)
+            accuracy = float((ids == ids_exact).float().mean().item())
+            ts = []
+            for _ in range(5):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                ctx.search(rs, d, pred, ids, paper=True)
+                e1.record()
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1) / 1e3)
+            t_search = float(np.median(ts))
+            # exact classification of the same window (fused kernel, graph replay)
+            for _ in range(2):
+                ctx.classify(rs, d, ids, path="fused_bf16", graph=True)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(3):
+                ctx.classify(rs, d, ids, path="fused_bf16", graph=True)
+            e1.record()
+            e1.synchronize()
+            fused = 3 * n / (e0.elapsed_time(e1) / 1e3) / 1e6
+            accesses = st_p["slot_reads"] + st_p["rule_reads"]
+            ctx.du_observe(rs, n, accesses)
+            win = ctx.du_close_window(rs, tau=tau, theta=theta)
+            row = {"window": w, "nn_accuracy": round(st_e["nn_correct"] / max(1, st_e["matched"]), 4),
+                   "paper_classification_accuracy": round(accuracy, 5),
+                   "paper_accesses_per_pkt": round(accesses / n, 3),
+                   "paper_probes_per_pkt": round(st_p["probes"] / n, 3),
+                   "search_paper_mpkts": round(n / t_search / 1e6, 1),
+                   "exact_probes_per_pkt": round(st_e["probes"] / n, 3), "fused_exact_mpkts": round(fused, 1),
+                   "drop_vs_base": round(1 - win["th_cur"] / win["th_base"], 4), "suboptimal": win["suboptimal"],
+                   "update_s": round(upd_s, 3), "decision": win["decision"]}
+            if mode == "iu_du" and win["decision"] != "none":
+                samples = wl.gen_trace(cur, [("inside", 1 << 18)], 3000 + w)
+                # incremental training starts from a trained model: a smaller step than from scratch
+                lr = 3e-4 if win["decision"] == "incremental" else 1e-3
+                rep = ctx.du_apply(rs, win["decision"], samples, N=HIDDEN, blocks=BLOCKS, batch=8192, epochs=1000,
+                                   max_rounds=1, alpha=100, holdout=0.05, time_budget_s=train_s, lr=lr, seed=64 + w)
+                row["du_train_s"] = round(rep["train_seconds"], 2)
+                row["du_holdout_accuracy"] = round(rep["holdout_accuracy"], 4)
+            rows.append(row)
+            del d, pred, ids, ids_exact
+        ctx.unload_ruleset(rs)
+        runs[mode] = rows
+    return {"rules": n_rules, "ruleset": "clustered: 64 (SIP /8, DIP /8) blocks, 97 % of a block's rules of its tuple",
+            "inserted": "the same draw with another seed (64 other blocks)", "windows": windows,
+            "deletes_and_inserts_per_window": per_window, "window_packets": window_packets, "tau": tau,
+            "theta": theta, "train_s_cap": train_s,
+            "monitored": "packets per memory access of the paper-mode search engine (stage 2 on the network's predictions)",
+            "runs": runs}
+
+
 def measure_peaks():
     """Denominators the driver's peak file lacks, measured with library GEMMs (cuBLAS SGEMM with
     TF32 off for FP32 SIMT; cuBLASLt E4M3 GEMM for FP8), best of a few 8192^3 runs."""
@@ -409,6 +515,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--train-seconds", type=float, default=float(os.environ.get("TANG_TRAIN_SECONDS", "20")))
     ap.add_argument("--quick", action="store_true", help="skip the secondary measurements")
+    ap.add_argument("--no-du", action="store_true", help="skip the deferred-update experiment")
     ap.add_argument("--packets", type=int, default=N_PACKETS, help="use the first P packets of the trace")
     ap.add_argument("--variant", default=None, choices=[None, "1sm", "2sm"],
                     help="tensor-core kernel variant (default: the library's choice)")
@@ -446,15 +553,15 @@ def main():
     ids = torch.empty(n, dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream()
 
-    def time_path(path, steps, warmup, graph=True):
+    def time_path(path, steps, warmup, graph=True, paper=False):
         for _ in range(warmup):
-            ctx.classify(rs, d_h, ids, path=path, graph=graph, variant=args.variant)
+            ctx.classify(rs, d_h, ids, path=path, graph=graph, variant=args.variant, paper=paper)
         torch.cuda.synchronize()
         barrier(world)
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
         for _ in range(steps):
-            ctx.classify(rs, d_h, ids, path=path, graph=graph, variant=args.variant)
+            ctx.classify(rs, d_h, ids, path=path, graph=graph, variant=args.variant, paper=paper)
         ev1.record(stream)
         torch.cuda.synchronize()
         barrier(world)
@@ -540,9 +647,19 @@ def main():
                                             "peak": pk2["fp32_simt_tflops"], "unit": "TFLOP/s",
                                             "frac": round(a32 / pk2["fp32_simt_tflops"], 4),
                                             "peak_kind": "cuBLAS SGEMM (TF32 off) 8192^3, burst (measured here)"}
+        # the paper's own post-verification (§5.1.1 as printed): speed and classification accuracy
+        dtpp = time_path("fused_bf16", args.steps, args.warmup, paper=True)
+        ids_paper = ids.cpu().numpy().view(np.uint32)
+        st_pp = ctx.classify(rs, d_h, ids, path="fused_bf16", stats=True, paper=True)
+        extra["paper_mode"] = {"fused_bf16_mpkts": round(n * args.steps / dtpp / 1e6, 3),
+                               "classification_accuracy": round(float((ids_paper == ids_fused).mean()), 6),
+                               "probes_per_pkt": round(st_pp["probes"] / n, 4),
+                               "rule_reads_per_pkt": round(st_pp["rule_reads"] / n, 4)}
         extra["stability"] = measure_stability(ctx)
         extra["serving"] = measure_serving(tg, ctx)
         extra["updates"] = measure_updates(tg, ctx)
+        if not args.no_du:
+            extra["deferred_update"] = measure_deferred_update(tg, ctx)
 
     # ---- e2e: host (pinned) buffers through the C ABI, copies inside the timed region
     ph = torch.empty(n * 16, dtype=torch.uint8, pin_memory=True).numpy()

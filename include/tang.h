@@ -1,11 +1,11 @@
 /*
  * tang.h -- C ABI of the B300 (sm_103a) TaNG packet classifier.
  *
- * TaNG classifies a packet header against a multi-field ruleset in two stages (§4.1.1): a
- * residual MLP (§5.1) predicts the tuple of the tuple space (§3.3) that holds the answer, then
+ * TaNG classifies a packet header against a multi-field ruleset in two stages (§5.1.1): a
+ * residual MLP (§6.1) predicts the tuple of the tuple space (§4.3) that holds the answer, then
  * that tuple's hash table is probed, the candidates are verified field by field, and the
  * highest-priority matching rule is returned. This library makes the post-verification exact
- * (the paper's is not: §4.1.1, §7): after a hit in the predicted tuple it also probes every tuple
+ * (the paper's is not: §5.1.1, §8): after a hit in the predicted tuple it also probes every tuple
  * that holds a better rule overlapping the hit, and after a miss it searches all other tuples in
  * ascending order of their best priority. The returned rule id is therefore always the one the
  * definition of §2.1 gives, whatever the network predicts.
@@ -90,13 +90,13 @@ const char *tang_last_error(tang_ctx *ctx);
 int tang_memory_usage(tang_ctx *ctx, size_t *used, size_t *cap);
 
 /* ---------------------------------------------------------------------------------------
- * Rulesets: tuple space (§3.3) + exactness certificate
+ * Rulesets: tuple space (§4.3) + exactness certificate
  * ------------------------------------------------------------------------------------- */
 
 /* Build the tuple space of `n` host rules and upload it. Tuples are the distinct
- * (sip_len, dip_len) pairs (§3.3: 5-field tuples are built from SIP and DIP), indexed in
+ * (sip_len, dip_len) pairs (§4.3: 5-field tuples are built from SIP and DIP), indexed in
  * order of first appearance over the rules sorted by (priority, id); a (0,0) tuple is
- * appended if absent so that restricted insertion (§4.2.1) always has a candidate.
+ * appended if absent so that restricted insertion (§5.2.1) always has a candidate.
  * Each tuple gets an open-addressing hash table keyed by the header truncated to the
  * tuple's lengths; the rules under one key form a run sorted by (priority, id).
  * Per rule, the conflict set (tuples holding a better rule that overlaps it) is computed
@@ -129,7 +129,7 @@ int tang_tuple_get(tang_ctx *ctx, uint32_t rs, uint32_t t, uint32_t *sip_len, ui
 int tang_rule_conflicts(tang_ctx *ctx, uint32_t rs, uint32_t id, uint32_t *tuple, uint32_t *words);
 
 /* ---------------------------------------------------------------------------------------
- * Model (§5.1): input FC (S=7 -> N) + k residual blocks (Eq. 1) + output FC (N -> C)
+ * Model (§6.1): input FC (S=7 -> N) + k residual blocks (Eq. 1) + output FC (N -> C)
  * ------------------------------------------------------------------------------------- */
 
 /* Precisions of the network's N x N layers. */
@@ -144,7 +144,7 @@ int tang_rule_conflicts(tang_ctx *ctx, uint32_t rs, uint32_t id, uint32_t *tuple
  *                                    all zero = "not calibrated", FP8 then refused)
  *   float params[] in this order, each row-major with the x.W convention of Eq. 1
  *     W0[S][N] b0[N]  { W1[N][N] b1[N] W2[N][N] b2[N] } x blocks  Wc[N][C] bc[C]
- * W0 acts on the raw 16-bit segment values of §5.2 (SIP hi, SIP lo, DIP hi, DIP lo, SP, DP,
+ * W0 acts on the raw 16-bit segment values of §6.2 (SIP hi, SIP lo, DIP hi, DIP lo, SP, DP,
  * PRO). */
 #define TANG_MODEL_MAGIC 0x474E4154u /* "TANG" */
 typedef struct tang_model_header {
@@ -157,12 +157,16 @@ typedef struct tang_model_header {
 /* Validate and upload a model for ruleset `rs`; keeps an FP32 copy and derives the BF16 and
  * (if calibrated) FP8 copies. Requires C == n_tuples, S == 7. The tensor-core paths further
  * require N == 512 (other N use the FP32 path only) and C <= 256.
- * Replaces a previous model of the ruleset. Synchronous.
+ * Replaces a previous model of the ruleset. Synchronous: waits for all work on the device.
+ * Hot swap (§5.2.2 deploys retrained weights while classification goes on): when the previous
+ * model has the same S, N, blocks, C and FP8 calibration state, the new weights are written into
+ * its device buffers, so CUDA graphs captured with TANG_GRAPH stay valid and their next replay
+ * uses the new model; otherwise the graphs are dropped and re-captured on their next call.
  * Errors: TANG_EINVAL (bad magic, sizes, C != T), TANG_ENOMEM. */
 int tang_load_model(tang_ctx *ctx, uint32_t rs, const void *blob, size_t bytes);
 
 /* ---------------------------------------------------------------------------------------
- * Classification (§4.1.1)
+ * Classification (§5.1.1)
  * ------------------------------------------------------------------------------------- */
 
 /* Path selection (flags & TANG_PATH_MASK). */
@@ -189,6 +193,12 @@ int tang_load_model(tang_ctx *ctx, uint32_t rs, const void *blob, size_t bytes);
 #define TANG_FUSED_MCAST4 0x1000  /* same with clusters of 4 CTAs */
 #define TANG_FUSED_N256 0x2000    /* one CTA per SM, 256-wide MMAs, single-buffered accumulator */
 #define TANG_VARIANT_MASK 0x3E00
+/* Post-verification exactly as §5.1.1 prints it, for measurement only: a match in the predicted
+ * tuple is returned at once, without the conflict-set probes, so a packet can get a
+ * lower-priority rule when the network predicts a wrong tuple that also holds a match (the case
+ * §5.1.1 and §8 leave uncorrected); a miss still searches the other tuples in order. Combines
+ * with every path; the default (flag clear) is the exact search. */
+#define TANG_SEARCH_PAPER 0x4000
 
 typedef struct tang_stats {
     uint64_t packets;       /* packets classified */
@@ -210,7 +220,7 @@ typedef struct tang_stats {
 int tang_classify(tang_ctx *ctx, uint32_t rs, const tang_header *headers, uint32_t n, uint32_t *ids,
                   uint32_t flags, void *stream, tang_stats *stats);
 
-/* Stage 1 alone (§4.1.1): run the network of ruleset rs over n device headers.
+/* Stage 1 alone (§5.1.1): run the network of ruleset rs over n device headers.
  * d_logits (device, n x C float, row-major; may be NULL) receives the output layer's logits;
  * d_tuple (device, n int32; may be NULL) the argmax (lowest index on ties).
  * precision: TANG_FP32 / TANG_BF16 / TANG_FP8, optionally OR-ed with TANG_FUSED_1SM or
@@ -223,6 +233,16 @@ int tang_infer(tang_ctx *ctx, uint32_t rs, const tang_header *d_headers, uint32_
  * [0, T) are treated as "no prediction". Writes d_ids (device). `stats` as in classify. */
 int tang_search(tang_ctx *ctx, uint32_t rs, const tang_header *d_headers, const int32_t *d_tuple, uint32_t n,
                 uint32_t *d_ids, void *stream, tang_stats *stats);
+
+/* tang_search with flags: 0 (exact search, same as tang_search) or TANG_SEARCH_PAPER.
+ * Errors as tang_search, plus TANG_EINVAL for unknown flag bits. */
+int tang_search_ex(tang_ctx *ctx, uint32_t rs, const tang_header *d_headers, const int32_t *d_tuple, uint32_t n,
+                   uint32_t *d_ids, uint32_t flags, void *stream, tang_stats *stats);
+
+/* Number of CUDA graphs the context holds for TANG_GRAPH replays. They are dropped when a
+ * ruleset is unloaded, the scratch buffer grows, or a model of another shape replaces a
+ * ruleset's model; a same-shape model swap (tang_load_model) keeps them. */
+int tang_graph_count(tang_ctx *ctx, uint32_t *count);
 
 /* Staged BF16 classification (the tensor-core network kernel, then the search kernel) for
  * callers that must not allocate device memory during a call: code running inside a custom
@@ -247,7 +267,7 @@ int tang_classify_noalloc(tang_ctx *ctx, uint32_t rs, const tang_header *d_heade
                           void *stream);
 
 /* ---------------------------------------------------------------------------------------
- * Immediate update (§4.2.1). Stream-ordered: every classify issued after the call (on any
+ * Immediate update (§5.2.1). Stream-ordered: every classify issued after the call (on any
  * stream) sees it. Neither call creates or removes a tuple, so a loaded model stays valid.
  * ------------------------------------------------------------------------------------- */
 
@@ -262,11 +282,12 @@ int tang_insert_rule(tang_ctx *ctx, uint32_t rs, const tang_rule *rule);
 int tang_delete_rule(tang_ctx *ctx, uint32_t rs, uint32_t id);
 
 /* Rules inserted since load whose lengths differ from their tuple's (the deferred-update
- * counter of §4.2.2). */
+ * counter of §5.2.2). */
 int tang_suboptimal_count(tang_ctx *ctx, uint32_t rs, uint64_t *count);
 
+
 /* ---------------------------------------------------------------------------------------
- * Training (§5.2), all on the GPU with this library's own forward/backward kernels
+ * Training (§6.2), all on the GPU with this library's own forward/backward kernels
  * ------------------------------------------------------------------------------------- */
 
 typedef struct tang_train_cfg {
@@ -292,8 +313,8 @@ typedef struct tang_train_report {
 } tang_train_report;
 
 /* Label n host sample headers with the tuple of their exact match (unmatched samples are
- * dropped), oversample every class below alpha, and train the network of §5.1 on it with
- * cross-entropy and Adam; repeat rounds with alpha x10 while holdout accuracy < beta (§5.2).
+ * dropped), oversample every class below alpha, and train the network of §6.1 on it with
+ * cross-entropy and Adam; repeat rounds with alpha x10 while holdout accuracy < beta (§6.2).
  * On success writes a model blob (calibrated FP8 amax included) to `blob` if *bytes is large
  * enough, and always sets *bytes to the blob size (call with blob == NULL to size it).
  * report may be NULL. Synchronous. */
@@ -311,6 +332,69 @@ int tang_loss_grad(tang_ctx *ctx, uint32_t S, uint32_t N, uint32_t blocks, uint3
 /* One Adam step (bias-corrected, step number t >= 1) over `count` host floats on the GPU. */
 int tang_adam_step(tang_ctx *ctx, float *params, const float *grads, float *m, float *v, uint64_t count,
                    uint32_t t, float lr, float beta1, float beta2, float eps);
+
+/* ---------------------------------------------------------------------------------------
+ * Deferred update (§5.2.2). A monitor on the search engine measures throughput per window;
+ * th_base is the first window closed after the last full retraining (or after load). When
+ * 1 - th_cur / th_base > tau, a deferred update is due: a full retraining if more than theta
+ * rules were inserted into a tuple whose lengths differ from theirs since the last full
+ * retraining (the tang_suboptimal_count counter), incremental training otherwise.
+ * ------------------------------------------------------------------------------------- */
+#define TANG_DU_NONE 0
+#define TANG_DU_INCREMENTAL 1
+#define TANG_DU_RETRAIN 2
+
+typedef struct tang_du_cfg {
+    double tau;     /* relative throughput drop that triggers (the paper's experiment: 0.05) */
+    uint64_t theta; /* counter value above which the update is a full retraining (paper: 10,000) */
+} tang_du_cfg;
+
+typedef struct tang_du_window {
+    uint64_t window;     /* index of the window just closed; 0 = the baseline window */
+    double th_cur;       /* its throughput: packets / cost */
+    double th_base;      /* baseline throughput */
+    uint64_t suboptimal; /* the counter when the window closed */
+    int decision;        /* TANG_DU_*; always TANG_DU_NONE for the baseline window */
+} tang_du_window;
+
+/* The decision rule alone: TANG_DU_NONE when th_base <= 0 or the drop 1 - th_cur / th_base
+ * does not exceed tau; else TANG_DU_RETRAIN when suboptimal > theta, else TANG_DU_INCREMENTAL.
+ * Needs no context and no GPU. Returns TANG_EINVAL for a NULL cfg or a negative/non-finite tau. */
+int tang_du_decide(const tang_du_cfg *cfg, double th_base, double th_cur, uint64_t suboptimal);
+
+/* Add an observation to ruleset rs's open window: `packets` classified at `cost` (any unit
+ * that grows with the search engine's work: seconds of the search kernel, or memory accesses
+ * from tang_stats; throughput is packets / cost, and only ratios of it matter). */
+int tang_du_observe(tang_ctx *ctx, uint32_t rs, uint64_t packets, double cost);
+
+/* Close the open window, evaluate the trigger and fill *out. The first window after load or
+ * after a full retraining becomes th_base. Errors: TANG_EINVAL (empty window, bad cfg). */
+int tang_du_close_window(tang_ctx *ctx, uint32_t rs, const tang_du_cfg *cfg, tang_du_window *out);
+
+/* Incremental training (§5.2.2): like tang_train, but the network starts from the ruleset's
+ * loaded model (its N and blocks; cfg->N and cfg->blocks are ignored) and the samples are
+ * labelled on the current tuple space, so the model follows the rules inserted and deleted
+ * since it was trained. Writes a blob as tang_train does; load it with tang_load_model (a hot
+ * swap, since the shape is unchanged). Errors: TANG_EINVAL (no model, or the model no longer
+ * fits the tuple count), and those of tang_train. */
+int tang_finetune(tang_ctx *ctx, uint32_t rs, const tang_header *samples, uint32_t n, const tang_train_cfg *cfg,
+                  void *blob, size_t *bytes, tang_train_report *report);
+
+/* Full rebuild of ruleset rs's tuple space over its live rules (the first step of a full
+ * retraining, §5.2.2): every rule moves to the tuple of its own lengths, tuples may appear or
+ * disappear (so T may change), conflict sets are recomputed, and the suboptimal counter and
+ * the monitor's baseline are reset. If the tuple list changed, the model is dropped (its
+ * classes no longer match) together with the context's graphs; *model_kept (may be NULL)
+ * says which happened. Synchronous. Errors: TANG_ENOMEM, TANG_ETABLEFULL. */
+int tang_rebuild_ruleset(tang_ctx *ctx, uint32_t rs, int *model_kept);
+
+/* Carry out a decision of tang_du_close_window: TANG_DU_NONE does nothing;
+ * TANG_DU_INCREMENTAL = tang_finetune + tang_load_model (hot swap); TANG_DU_RETRAIN =
+ * tang_rebuild_ruleset + tang_train from scratch (cfg's N and blocks) + tang_load_model.
+ * `samples` are recent packet headers (host, n of them); cfg->time_budget_s caps the training
+ * time. Synchronous. */
+int tang_du_apply(tang_ctx *ctx, uint32_t rs, int decision, const tang_header *samples, uint32_t n,
+                  const tang_train_cfg *cfg, tang_train_report *report);
 
 /* ---------------------------------------------------------------------------------------
  * Autotuning and serving

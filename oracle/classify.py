@@ -41,3 +41,30 @@ def classify(rules: np.ndarray, headers: np.ndarray, threads: int | None = None,
     if rc != 0:
         raise MemoryError("oracle_classify failed")
     return (ids, idx) if return_index else ids
+
+
+def paper_classify(rules: np.ndarray, headers: np.ndarray, predicted, tuple_of_rule, threads: int | None = None):
+    """§5.1.1's post-verification exactly as the paper states it (it is not exact).
+
+    Per packet: if some rule stored in the predicted tuple matches, the answer is the
+    highest-priority such rule (the search stays in that tuple, even when a better rule of another
+    tuple also matches: the first scenario of §5.1.1, left uncorrected per §8). Otherwise the
+    ordered search over the remaining tuples runs, and since the predicted tuple holds no match
+    its result is the highest-priority match over all rules, i.e. the §2.1 answer.
+    predicted[i] outside [0, T) means no prediction. tuple_of_rule[j] is the tuple rules[j] is
+    stored in. Written as that definition over the linear scan, not as the search procedure.
+    """
+    rules = np.ascontiguousarray(rules, dtype=RULE_DTYPE)
+    headers = np.ascontiguousarray(headers, dtype=HEADER_DTYPE)
+    pred = np.asarray(predicted, dtype=np.int64)
+    tor = np.asarray(tuple_of_rule, dtype=np.int64)
+    out = classify(rules, headers, threads)
+    for t in np.unique(pred):
+        members = rules[tor == t]
+        if t < 0 or len(members) == 0:
+            continue
+        sel = np.nonzero(pred == t)[0]
+        inside = classify(members, headers[sel], threads)
+        hit = inside != NO_MATCH
+        out[sel[hit]] = inside[hit]
+    return out

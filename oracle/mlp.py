@@ -1,15 +1,15 @@
 """ORACLE (test infrastructure): TaNG's residual MLP in float64, its gradients, and its training math.
 
 Sources in the paper:
-  §5.2  feature encoding: the header is cut into 16-bit segments, each taken as a float. A 5-field
+  §6.2  feature encoding: the header is cut into 16-bit segments, each taken as a float. A 5-field
         header gives 7 segments: SIP high/low, DIP high/low, SP, DP, PRO.
-  §5.1  network: an input FC layer (S -> N), k residual blocks of two N x N FC layers, an output
+  §6.1  network: an input FC layer (S -> N), k residual blocks of two N x N FC layers, an output
         FC layer (N -> C), ReLU activations throughout, argmax over the outputs.
   Eq. 1 residual block. The printed equation has unbalanced parentheses; the reading used here is
         B(x) = ReLU( ReLU(x W1 + b1) W2 + b2 + x ), i.e. the skip connection is added before the
         block's last activation.
   Eq. 2 A(z) = max(0, z).
-  §5.2  training: cross-entropy loss and the Adam optimiser (PyTorch defaults: beta1 0.9,
+  §6.2  training: cross-entropy loss and the Adam optimiser (PyTorch defaults: beta1 0.9,
         beta2 0.999, eps 1e-8).
 
 Weights follow the x . W convention of Eq. 1: W has shape (inputs, outputs).
@@ -23,7 +23,7 @@ S_FEATURES = 7
 
 
 def features(headers: np.ndarray) -> np.ndarray:
-    """§5.2 encoding: (n, 7) float64 of the 16-bit segments (exact in float32 and float64)."""
+    """§6.2 encoding: (n, 7) float64 of the 16-bit segments (exact in float32 and float64)."""
     sip = headers["sip"].astype(np.int64)
     dip = headers["dip"].astype(np.int64)
     return np.stack(

@@ -1,13 +1,13 @@
 """ORACLE (test infrastructure): tuple space, restricted insertion and overlap-conflict sets.
 
 Sources in the paper:
-  §3.3  tuples group rules by their prefix-length vector; for 5-field rules the tuples are built
+  §4.3  tuples group rules by their prefix-length vector; for 5-field rules the tuples are built
         from SIP and DIP lengths only; a rule is truncated to its tuple's lengths (zero the bits
         below the length) and stored in that tuple's hash table under the truncated key.
-  §4.2.1 restricted insertion: use the tuple whose lengths equal the rule's; otherwise, among the
+  §5.2.1 restricted insertion: use the tuple whose lengths equal the rule's; otherwise, among the
         tuples whose lengths are all <= the rule's, the first one with the largest length sum.
-  §4.1.1 post-verification searches the remaining tuples when the predicted tuple has no match,
-        and (§4.1.1, §7) leaves a lower-priority hit in a wrong tuple uncorrected. The conflict
+  §5.1.1 post-verification searches the remaining tuples when the predicted tuple has no match,
+        and (§5.1.1, §8) leaves a lower-priority hit in a wrong tuple uncorrected. The conflict
         sets below close that gap: conflict(r) holds the tuple of every rule that beats r and
         shares at least one header with r. If P matches r, the true answer lies in r's tuple or
         in a tuple of conflict(r), because the true answer also contains P.
@@ -27,7 +27,7 @@ def prefix_mask(length: int) -> int:
 
 
 def truncate(value: int, length: int) -> int:
-    """§3.3 truncation of a prefix value to a tuple's length."""
+    """§4.3 truncation of a prefix value to a tuple's length."""
     return value & prefix_mask(length)
 
 
@@ -37,7 +37,7 @@ def priority_order(rules: np.ndarray) -> np.ndarray:
 
 
 def build_tuples(rules: np.ndarray, ensure_zero_tuple: bool = True):
-    """§3.3 tuple construction. Returns (tuples, tuple_of_rule).
+    """§4.3 tuple construction. Returns (tuples, tuple_of_rule).
 
     tuples[t] = (sip_len, dip_len); tuple_of_rule[i] = t for rules[i].
     """
@@ -67,7 +67,7 @@ def tuple_buckets(rules: np.ndarray, tuples, tuple_of_rule):
 
 
 def restricted_insert_tuple(tuples, sip_len: int, dip_len: int):
-    """§4.2.1: exact-length tuple if present, else the first tuple with l^T <= l^R of maximal sum.
+    """§5.2.1: exact-length tuple if present, else the first tuple with l^T <= l^R of maximal sum.
 
     Returns the tuple index, or None when no tuple satisfies l^T <= l^R.
     """
@@ -82,7 +82,7 @@ def restricted_insert_tuple(tuples, sip_len: int, dip_len: int):
 
 
 def insertion_candidates(tuples, sip_len: int, dip_len: int):
-    """All tuples with l^T <= l^R componentwise (§4.2.1)."""
+    """All tuples with l^T <= l^R componentwise (§5.2.1)."""
     return [t for t, (ls, ld) in enumerate(tuples) if ls <= sip_len and ld <= dip_len]
 
 
@@ -140,7 +140,7 @@ def conflict_words(rules: np.ndarray, tuple_of_rule, n_tuples: int) -> np.ndarra
 
 
 class TwoStageSearch:
-    """Two-stage search of §4.1.1 made exact with the conflict sets (a plain restatement).
+    """Two-stage search of §5.1.1 made exact with the conflict sets (a plain restatement).
 
     1. Probe the predicted tuple: truncate the header to the tuple's lengths, look up that key,
        compare the bucket's rules one by one; the first match is the tuple's best.

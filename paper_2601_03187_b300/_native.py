@@ -29,6 +29,9 @@ PATHS = {
 MEM_DEVICE, MEM_HOST, GRAPH = 0x00, 0x10, 0x100
 FUSED_1SM, FUSED_2SM, FUSED_MCAST2, FUSED_MCAST4, FUSED_N256 = 0x200, 0x400, 0x800, 0x1000, 0x2000
 VARIANTS = {None: 0, "1sm": FUSED_1SM, "2sm": FUSED_2SM, "mc2": FUSED_MCAST2, "mc4": FUSED_MCAST4, "n256": FUSED_N256}
+SEARCH_PAPER = 0x4000
+DU_NONE, DU_INCREMENTAL, DU_RETRAIN = 0, 1, 2
+DU_DECISIONS = {DU_NONE: "none", DU_INCREMENTAL: "incremental", DU_RETRAIN: "retrain"}
 MODEL_MAGIC = 0x474E4154
 MODEL_HEADER_BYTES = 64
 
@@ -65,6 +68,15 @@ class TrainReport(ctypes.Structure):
                 ("samples_trained", ctypes.c_uint32), ("classes_empty", ctypes.c_uint32),
                 ("alpha_final", ctypes.c_uint32), ("final_loss", ctypes.c_float),
                 ("holdout_accuracy", ctypes.c_float), ("train_seconds", ctypes.c_float)]
+
+
+class DuCfg(ctypes.Structure):
+    _fields_ = [("tau", ctypes.c_double), ("theta", ctypes.c_uint64)]
+
+
+class DuWindow(ctypes.Structure):
+    _fields_ = [("window", ctypes.c_uint64), ("th_cur", ctypes.c_double), ("th_base", ctypes.c_double),
+                ("suboptimal", ctypes.c_uint64), ("decision", ctypes.c_int)]
 
 
 class ServeCfg(ctypes.Structure):
@@ -104,6 +116,14 @@ _SIGS = {
     "tang_serve_stop": (_I, [_P]),
     "tang_now": (ctypes.c_double, []),
     "tang_classify_noalloc": (_I, [_P, _U32, _P, _U32, _P, _P]),
+    "tang_search_ex": (_I, [_P, _U32, _P, _P, _U32, _P, _U32, _P, ctypes.POINTER(Stats)]),
+    "tang_graph_count": (_I, [_P, ctypes.POINTER(_U32)]),
+    "tang_du_decide": (_I, [ctypes.POINTER(DuCfg), ctypes.c_double, ctypes.c_double, _U64]),
+    "tang_du_observe": (_I, [_P, _U32, _U64, ctypes.c_double]),
+    "tang_du_close_window": (_I, [_P, _U32, ctypes.POINTER(DuCfg), ctypes.POINTER(DuWindow)]),
+    "tang_finetune": (_I, [_P, _U32, _P, _U32, ctypes.POINTER(TrainCfg), _P, ctypes.POINTER(_SZ), ctypes.POINTER(TrainReport)]),
+    "tang_rebuild_ruleset": (_I, [_P, _U32, ctypes.POINTER(_I)]),
+    "tang_du_apply": (_I, [_P, _U32, _I, _P, _U32, ctypes.POINTER(TrainCfg), ctypes.POINTER(TrainReport)]),
 }
 
 
@@ -288,14 +308,18 @@ class Context:
         self._ck(lib.tang_load_model(self._h, rs, buf, len(blob)), "load_model")
 
     # -- classification ---------------------------------------------------------------------
-    def classify(self, rs: int, headers, ids, path="fused_bf16", graph=False, stream=None, stats=False, variant=None):
+    def classify(self, rs: int, headers, ids, path="fused_bf16", graph=False, stream=None, stats=False, variant=None,
+                 paper=False):
         """ids[i] = matching rule id. numpy headers/ids -> host mode; torch CUDA tensors -> device mode.
-        variant: None (tuned / default), "1sm" or "2sm" tensor-core kernel."""
+        variant: None (tuned / default), "1sm" or "2sm" tensor-core kernel. paper: the paper's
+        non-exact post-verification (TANG_SEARCH_PAPER), for measurement."""
         host = isinstance(headers, np.ndarray)
         flags = (PATHS[path] if isinstance(path, str) else int(path)) | VARIANTS[variant]
         flags |= MEM_HOST if host else MEM_DEVICE
         if graph:
             flags |= GRAPH
+        if paper:
+            flags |= SEARCH_PAPER
         n = _n_headers(headers)
         st = Stats()
         self._ck(lib.tang_classify(self._h, rs, _ptr(headers), n, _ptr(ids), flags,
@@ -308,12 +332,18 @@ class Context:
         self._ck(lib.tang_infer(self._h, rs, _ptr(headers), n, _ptr(logits), _ptr(tuples),
                                 precision | VARIANTS[variant], _stream(stream)), "infer")
 
-    def search(self, rs: int, headers, tuples, ids, stream=None, stats=False):
+    def search(self, rs: int, headers, tuples, ids, stream=None, stats=False, paper=False):
         n = _n_headers(headers)
         st = Stats()
-        self._ck(lib.tang_search(self._h, rs, _ptr(headers), _ptr(tuples), n, _ptr(ids), _stream(stream),
-                                 ctypes.byref(st) if stats else None), "search")
+        self._ck(lib.tang_search_ex(self._h, rs, _ptr(headers), _ptr(tuples), n, _ptr(ids),
+                                    SEARCH_PAPER if paper else 0, _stream(stream),
+                                    ctypes.byref(st) if stats else None), "search")
         return st.as_dict() if stats else None
+
+    def graph_count(self) -> int:
+        c = ctypes.c_uint32()
+        self._ck(lib.tang_graph_count(self._h, ctypes.byref(c)), "graph_count")
+        return c.value
 
     def classify_noalloc(self, rs: int, headers, ids, stream=None):
         """Staged BF16 classify whose inter-kernel scratch is a static device array (no allocation)."""
@@ -335,20 +365,69 @@ class Context:
         return c.value
 
     # -- training ---------------------------------------------------------------------------
-    def train(self, rs: int, samples: np.ndarray, **cfg):
+    @staticmethod
+    def _train_cfg(cfg):
         c = TrainCfg(N=512, blocks=6, batch=8192, epochs=1000, max_rounds=3, decay_every=200, lr=1e-3, decay=0.1,
                      alpha=1000, beta=0.95, holdout=0.1, time_budget_s=0.0, seed=0)
         for k, v in cfg.items():
             setattr(c, k, v)
+        return c
+
+    def _train_call(self, fn, what, rs, samples, c):
         samples = np.ascontiguousarray(samples, dtype=HEADER_DTYPE)
+        size = ctypes.c_size_t(0)
+        rep = TrainReport()
+        # size query first (blob == NULL), then the real call into a buffer of that size
+        buf = None
+        for _ in range(2):
+            self._ck(fn(self._h, rs, samples.ctypes.data, len(samples), ctypes.byref(c), buf, ctypes.byref(size),
+                        ctypes.byref(rep)), what)
+            if buf is not None:
+                break
+            buf = ctypes.create_string_buffer(size.value)
+        return buf.raw[: size.value], {k: getattr(rep, k) for k, _ in rep._fields_}
+
+    def train(self, rs: int, samples: np.ndarray, **cfg):
+        c = self._train_cfg(cfg)
         T = self.ruleset_info(rs)["n_tuples"]
         nparams = 7 * c.N + c.N + c.blocks * (2 * c.N * c.N + 2 * c.N) + c.N * T + T
         size = ctypes.c_size_t(MODEL_HEADER_BYTES + 4 * (2 * c.blocks + 1) + 4 * nparams)
         buf = ctypes.create_string_buffer(size.value)
         rep = TrainReport()
+        samples = np.ascontiguousarray(samples, dtype=HEADER_DTYPE)
         self._ck(lib.tang_train(self._h, rs, samples.ctypes.data, len(samples), ctypes.byref(c), buf,
                                 ctypes.byref(size), ctypes.byref(rep)), "train")
         return buf.raw[: size.value], {k: getattr(rep, k) for k, _ in rep._fields_}
+
+    def finetune(self, rs: int, samples: np.ndarray, **cfg):
+        """Incremental training from the ruleset's loaded model (tang_finetune): (blob, report)."""
+        return self._train_call(lib.tang_finetune, "finetune", rs, samples, self._train_cfg(cfg))
+
+    # -- deferred update (§5.2.2) -----------------------------------------------------------
+    def rebuild_ruleset(self, rs: int) -> bool:
+        """Rebuild the tuple space over the live rules; True if the loaded model was kept."""
+        kept = ctypes.c_int()
+        self._ck(lib.tang_rebuild_ruleset(self._h, rs, ctypes.byref(kept)), "rebuild_ruleset")
+        return bool(kept.value)
+
+    def du_observe(self, rs: int, packets: int, cost: float):
+        self._ck(lib.tang_du_observe(self._h, rs, int(packets), float(cost)), "du_observe")
+
+    def du_close_window(self, rs: int, tau: float = 0.05, theta: int = 10000) -> dict:
+        c = DuCfg(tau=tau, theta=theta)
+        w = DuWindow()
+        self._ck(lib.tang_du_close_window(self._h, rs, ctypes.byref(c), ctypes.byref(w)), "du_close_window")
+        return {"window": w.window, "th_cur": w.th_cur, "th_base": w.th_base, "suboptimal": w.suboptimal,
+                "decision": DU_DECISIONS[w.decision]}
+
+    def du_apply(self, rs: int, decision, samples: np.ndarray, **cfg) -> dict:
+        d = {v: k for k, v in DU_DECISIONS.items()}[decision] if isinstance(decision, str) else int(decision)
+        c = self._train_cfg(cfg)
+        samples = np.ascontiguousarray(samples, dtype=HEADER_DTYPE)
+        rep = TrainReport()
+        self._ck(lib.tang_du_apply(self._h, rs, d, samples.ctypes.data, len(samples), ctypes.byref(c),
+                                   ctypes.byref(rep)), "du_apply")
+        return {k: getattr(rep, k) for k, _ in rep._fields_}
 
     def loss_grad(self, S, N, blocks, C, params: np.ndarray, headers: np.ndarray, labels: np.ndarray, input_scale=1.0):
         params = np.ascontiguousarray(params, dtype=np.float32)
@@ -398,3 +477,12 @@ class Context:
 
 def now() -> float:
     return lib.tang_now()
+
+
+def du_decide(tau: float, theta: int, th_base: float, th_cur: float, suboptimal: int) -> str:
+    """The deferred-update rule of §5.2.2 (tang_du_decide): "none", "incremental" or "retrain"."""
+    c = DuCfg(tau=tau, theta=theta)
+    rc = lib.tang_du_decide(ctypes.byref(c), float(th_base), float(th_cur), int(suboptimal))
+    if rc < 0:
+        raise TangError(rc, "tang_du_decide: bad configuration")
+    return DU_DECISIONS[rc]

@@ -290,6 +290,43 @@ void tang_model_free(tang_ctx *ctx, DeviceModel *m) {
     m->d_params = nullptr;
 }
 
+// Bytes of a buffer allocated through ctx_alloc (0 if unknown or null).
+static size_t alloc_size(tang_ctx *ctx, const void *p) {
+    if (!p) return 0;
+    std::lock_guard<std::mutex> g(ctx->alloc_mu);
+    auto it = ctx->allocs.find(const_cast<void *>(p));
+    return it == ctx->allocs.end() ? 0 : it->second;
+}
+
+static int check_cuda(tang_ctx *ctx, const char *what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return set_err(ctx, TANG_EDEVICE, "%s: %s", what, cudaGetErrorString(e));
+    return TANG_OK;
+}
+
+// Hot swap of a model between graph replays: when the new model has the live one's shape and
+// buffer set, its device copies are written over the live buffers, so every pointer and tensor
+// map that launches (and captured CUDA graphs) hold stays valid. All device work is drained
+// first, so no kernel reads a half-written model. Returns false (nothing changed) otherwise.
+static bool swap_in_place(tang_ctx *ctx, DeviceModel &live, const DeviceModel &next) {
+    if (live.S != next.S || live.N != next.N || live.blocks != next.blocks || live.C != next.C ||
+        live.Cpad != next.Cpad || live.has_fp8 != next.has_fp8)
+        return false;
+    const void *dst[] = {live.d_params, live.d_wbf16, live.d_wfp8, live.d_wscale8, live.d_bias_tc, live.d_fold8, live.d_l0};
+    const void *src[] = {next.d_params, next.d_wbf16, next.d_wfp8, next.d_wscale8, next.d_bias_tc, next.d_fold8, next.d_l0};
+    for (int k = 0; k < 7; ++k)
+        if ((dst[k] == nullptr) != (src[k] == nullptr) || alloc_size(ctx, dst[k]) != alloc_size(ctx, src[k])) return false;
+    cudaDeviceSynchronize();
+    for (int k = 0; k < 7; ++k)
+        if (dst[k]) cudaMemcpyAsync(const_cast<void *>(dst[k]), src[k], alloc_size(ctx, src[k]), cudaMemcpyDeviceToDevice,
+                                    ctx->stream);
+    cudaStreamSynchronize(ctx->stream);
+    live.host_params = next.host_params;
+    std::memcpy(live.act_amax, next.act_amax, sizeof(live.act_amax));
+    std::memcpy(live.act_scale, next.act_scale, sizeof(live.act_scale));
+    return true;
+}
+
 int tang_load_model(tang_ctx *ctx, uint32_t rsh, const void *blob, size_t bytes) {
     if (!ctx || !blob) return set_err(ctx, TANG_EINVAL, "null argument");
     Ruleset *rs = find_rs(ctx, rsh);
@@ -309,7 +346,6 @@ int tang_load_model(tang_ctx *ctx, uint32_t rsh, const void *blob, size_t bytes)
     if (bytes != want) return set_err(ctx, TANG_EINVAL, "model blob has %zu bytes, expected %zu", bytes, want);
     cudaSetDevice(ctx->device);
     CK(cudaStreamSynchronize(ctx->stream));
-    drop_graphs(ctx);
     std::unique_ptr<DeviceModel> m(new DeviceModel());
     m->S = hd.S;
     m->N = hd.N;
@@ -356,6 +392,13 @@ int tang_load_model(tang_ctx *ctx, uint32_t rsh, const void *blob, size_t bytes)
             return rc;
         }
     }
+    if (rs->model && swap_in_place(ctx, *rs->model, *m)) {
+        // the live buffers now hold the new weights; the staging copy goes
+        tang_model_free(ctx, m.get());
+        return check_cuda(ctx, "model swap");
+    }
+    cudaDeviceSynchronize();
+    drop_graphs(ctx);  // graphs captured the old model's buffers
     if (rs->model) tang_model_free(ctx, rs->model.get());
     rs->model = std::move(m);
     return TANG_OK;
@@ -379,7 +422,7 @@ static int run_infer(tang_ctx *ctx, Ruleset &rs, const tang_header *h, uint32_t 
 
 // Enqueue the device-resident classification of one batch on `st` (no synchronisation).
 static int enqueue_classify(tang_ctx *ctx, Ruleset &rs, const tang_header *h, uint32_t n, uint32_t *ids,
-                            uint32_t path, DevStats *stats, cudaStream_t st, int variant = 0) {
+                            uint32_t path, DevStats *stats, cudaStream_t st, int variant = 0, bool paper = false) {
     if (n == 0) return TANG_OK;
     const int cw = int(rs.host.cw);
     const TuneEntry *tune = nullptr;
@@ -388,7 +431,7 @@ static int enqueue_classify(tang_ctx *ctx, Ruleset &rs, const tang_header *h, ui
     switch (path) {
         case TANG_PATH_NO_NN: {
             cudaError_t e = launch_search(rs.d_desc, uint32_t(rs.host.tuples.size()), cw, h, nullptr, n, ids, stats,
-                                          tune, st);
+                                          tune, st, paper);
             if (e != cudaSuccess) return set_err(ctx, TANG_EDEVICE, "search: %s", cudaGetErrorString(e));
             return TANG_OK;
         }
@@ -412,7 +455,7 @@ static int enqueue_classify(tang_ctx *ctx, Ruleset &rs, const tang_header *h, ui
                 rc = run_infer(ctx, rs, h + c0, rows, nullptr, tup, prec, st, variant);
                 if (rc) return rc;
                 cudaError_t e = launch_search(rs.d_desc, uint32_t(rs.host.tuples.size()), cw, h + c0, tup, rows,
-                                              ids + c0, stats, tune, st);
+                                              ids + c0, stats, tune, st, paper);
                 if (e != cudaSuccess) return set_err(ctx, TANG_EDEVICE, "search: %s", cudaGetErrorString(e));
             }
             return TANG_OK;
@@ -424,7 +467,7 @@ static int enqueue_classify(tang_ctx *ctx, Ruleset &rs, const tang_header *h, ui
             const int prec = path == TANG_PATH_FUSED_BF16 ? TANG_BF16 : TANG_FP8;
             if (prec == TANG_FP8 && !rs.model->has_fp8)
                 return set_err(ctx, TANG_EINVAL, "FP8 path needs a calibrated model (act_amax)");
-            return tc_launch(ctx, rs, h, n, ids, nullptr, nullptr, prec, true, stats, st, tune, variant);
+            return tc_launch(ctx, rs, h, n, ids, nullptr, nullptr, prec, true, stats, st, tune, variant, paper);
         }
         default:
             return set_err(ctx, TANG_EINVAL, "unknown path %u", path);
@@ -432,7 +475,7 @@ static int enqueue_classify(tang_ctx *ctx, Ruleset &rs, const tang_header *h, ui
 }
 
 static int classify_host(tang_ctx *ctx, Ruleset &rs, const tang_header *h, uint32_t n, uint32_t *ids, uint32_t path,
-                         DevStats *stats, int variant);
+                         DevStats *stats, int variant, bool paper);
 
 
 int tang_classify(tang_ctx *ctx, uint32_t rsh, const tang_header *headers, uint32_t n, uint32_t *ids, uint32_t flags,
@@ -445,29 +488,30 @@ int tang_classify(tang_ctx *ctx, uint32_t rsh, const tang_header *headers, uint3
         return set_err(ctx, TANG_EINVAL, "headers must be 16-byte aligned and ids 4-byte aligned");
     const uint32_t path = flags & TANG_PATH_MASK;
     const int variant = variant_of(flags);
+    const bool paper = (flags & TANG_SEARCH_PAPER) != 0;
     cudaSetDevice(ctx->device);
     cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : ctx->stream;
     DevStats *dst = stats ? ctx->d_stats : nullptr;
     if (dst) CK(cudaMemsetAsync(dst, 0, sizeof(DevStats), st));
     int rc;
     if (flags & TANG_MEM_HOST) {
-        rc = classify_host(ctx, *rs, headers, n, ids, path, dst, variant);
+        rc = classify_host(ctx, *rs, headers, n, ids, path, dst, variant, paper);
     } else {
         if (rs->has_update) CK(cudaStreamWaitEvent(st, rs->last_update, 0));
         if ((flags & TANG_GRAPH) && !dst && n) {
-            GraphKey key{rsh, path | uint32_t(variant) << 8, n, headers, ids, (void *)st};
+            GraphKey key{rsh, path | uint32_t(variant) << 8 | uint32_t(paper) << 16, n, headers, ids, (void *)st};
             auto it = ctx->graphs.find(key);
             if (it == ctx->graphs.end()) {
                 // First call for this key: run eagerly (this sizes any scratch, so nothing
                 // allocates or synchronises inside the capture), then capture for later calls.
-                rc = enqueue_classify(ctx, *rs, headers, n, ids, path, nullptr, st, variant);
+                rc = enqueue_classify(ctx, *rs, headers, n, ids, path, nullptr, st, variant, paper);
                 if (rc) return rc;
                 CK(cudaStreamSynchronize(st));
                 // capture on a private stream so the caller's stream may be the legacy one
                 cudaStream_t cap;
                 CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
                 CK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
-                rc = enqueue_classify(ctx, *rs, headers, n, ids, path, nullptr, cap, variant);
+                rc = enqueue_classify(ctx, *rs, headers, n, ids, path, nullptr, cap, variant, paper);
                 cudaGraph_t g = nullptr;
                 cudaError_t e = cudaStreamEndCapture(cap, &g);
                 cudaStreamDestroy(cap);
@@ -486,7 +530,7 @@ int tang_classify(tang_ctx *ctx, uint32_t rsh, const tang_header *headers, uint3
             }
             rc = TANG_OK;
         } else {
-            rc = enqueue_classify(ctx, *rs, headers, n, ids, path, dst, st, variant);
+            rc = enqueue_classify(ctx, *rs, headers, n, ids, path, dst, st, variant, paper);
         }
     }
     if (rc) return rc;
@@ -511,7 +555,7 @@ int tang_classify(tang_ctx *ctx, uint32_t rsh, const tang_header *headers, uint3
 // D2H (copy_out stream) through two device buffers, so copies of one chunk overlap the
 // compute of the next. Pageable user buffers are staged through pinned buffers by this thread.
 static int classify_host(tang_ctx *ctx, Ruleset &rs, const tang_header *h, uint32_t n, uint32_t *ids, uint32_t path,
-                         DevStats *stats, int variant) {
+                         DevStats *stats, int variant, bool paper) {
     if (n == 0) return TANG_OK;
     const uint32_t chunk = std::min<uint32_t>(n, 1u << 20);
     if (ctx->dev_pkts < chunk) {
@@ -577,7 +621,7 @@ static int classify_host(tang_ctx *ctx, Ruleset &rs, const tang_header *h, uint3
         cudaEventRecord(ev_in[b], ctx->copy_in);
         cudaStreamWaitEvent(ctx->stream, ev_in[b], 0);
         rc = enqueue_classify(ctx, rs, dh + size_t(b) * chunk, rows, di + size_t(b) * chunk, path, stats, ctx->stream,
-                              variant);
+                              variant, paper);
         cudaEventRecord(ev_comp[b], ctx->stream);
         cudaStreamWaitEvent(ctx->copy_out, ev_comp[b], 0);
         uint32_t *dst = pinned ? ids + c0 : pi + size_t(b) * chunk;
@@ -618,6 +662,11 @@ int tang_infer(tang_ctx *ctx, uint32_t rsh, const tang_header *d_headers, uint32
 
 int tang_search(tang_ctx *ctx, uint32_t rsh, const tang_header *d_headers, const int32_t *d_tuple, uint32_t n,
                 uint32_t *d_ids, void *stream, tang_stats *stats) {
+    return tang_search_ex(ctx, rsh, d_headers, d_tuple, n, d_ids, 0, stream, stats);
+}
+
+int tang_search_ex(tang_ctx *ctx, uint32_t rsh, const tang_header *d_headers, const int32_t *d_tuple, uint32_t n,
+                   uint32_t *d_ids, uint32_t flags, void *stream, tang_stats *stats) {
     if (!ctx) return TANG_EINVAL;
     Ruleset *rs = find_rs(ctx, rsh);
     if (!rs) return set_err(ctx, TANG_ENOTFOUND, "unknown ruleset %u", rsh);
@@ -628,8 +677,9 @@ int tang_search(tang_ctx *ctx, uint32_t rsh, const tang_header *d_headers, const
     if (rs->has_update) CK(cudaStreamWaitEvent(st, rs->last_update, 0));
     DevStats *dst = stats ? ctx->d_stats : nullptr;
     if (dst) CK(cudaMemsetAsync(dst, 0, sizeof(DevStats), st));
+    if (flags & ~uint32_t(TANG_SEARCH_PAPER)) return set_err(ctx, TANG_EINVAL, "unknown search flags 0x%x", flags);
     CK(launch_search(rs->d_desc, uint32_t(rs->host.tuples.size()), rs->host.cw, d_headers, d_tuple, n, d_ids, dst,
-                     nullptr, st));
+                     nullptr, st, (flags & TANG_SEARCH_PAPER) != 0));
     if (stats) {
         DevStats hs;
         CK(cudaMemcpyAsync(&hs, dst, sizeof(hs), cudaMemcpyDeviceToHost, st));

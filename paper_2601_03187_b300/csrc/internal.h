@@ -26,7 +26,7 @@ constexpr uint32_t kMaxTuples = 2047;  // tuple index is stored in 11 bits of a 
 // Device records. All are read with 16-byte vector loads, so sizes are multiples of 16.
 // ---------------------------------------------------------------------------------------
 
-// One tuple (§3.3): truncation masks, its open-addressing table, its best (priority, id).
+// One tuple (§4.3): truncation masks, its open-addressing table, its best (priority, id).
 struct TupleDesc {
     uint32_t mask_s, mask_d;      // prefix masks of the tuple's SIP / DIP lengths
     uint32_t slot_base, slot_mask; // table = slots[slot_base .. slot_base + slot_mask]
@@ -104,7 +104,7 @@ struct HostTSS {
     std::vector<uint16_t> order;      // search order
     uint32_t cw = 1;
     uint32_t live = 0;
-    uint64_t suboptimal = 0;          // inserts whose lengths differ from their tuple's (§4.2.2 counter)
+    uint64_t suboptimal = 0;          // inserts whose lengths differ from their tuple's (§5.2.2 counter)
     int16_t tuple_of_len[33][33];     // (sip_len, dip_len) -> tuple index or -1
 };
 
@@ -178,6 +178,12 @@ struct Ruleset {
     bool has_update = false;
     double build_ms = 0;
     std::map<uint32_t, TuneEntry> tune;  // per path
+    // deferred-update monitor (§5.2.2): the open window's packets and cost, and the throughput of
+    // the first window closed after the last full retraining (windows == 0: not measured yet)
+    uint64_t du_packets = 0;
+    double du_cost = 0.0;
+    uint64_t du_windows = 0;
+    double du_th_base = 0.0;
 };
 
 struct ServeEngine;
@@ -225,6 +231,7 @@ int tss_upload(tang_ctx *ctx, Ruleset &rs, cudaStream_t st);
 int tss_insert(tang_ctx *ctx, Ruleset &rs, const tang_rule &r, cudaStream_t st);
 int tss_delete(tang_ctx *ctx, Ruleset &rs, uint32_t id, cudaStream_t st);
 void tss_free(tang_ctx *ctx, Ruleset &rs);
+int tss_rebuild(tang_ctx *ctx, Ruleset &rs, bool &same_tuples);
 uint64_t fmix64_host(uint64_t k);
 
 // search.cu
@@ -236,7 +243,7 @@ cudaError_t launch_run_shift(DRule *pool, uint32_t start, uint32_t len, uint32_t
 cudaError_t launch_run_copy(DRule *pool, uint32_t from, uint32_t to, uint32_t len, cudaStream_t st);
 cudaError_t launch_search(const Tables *d_desc, uint32_t T, uint32_t cw, const tang_header *h,
                           const int32_t *tuple, uint32_t n, uint32_t *ids, DevStats *stats, const TuneEntry *tune,
-                          cudaStream_t st);
+                          cudaStream_t st, bool paper = false);
 
 // mlp_simt.cu (FP32 CUDA-core kernels: plain path and trainer)
 cudaError_t launch_encode(const tang_header *h, uint32_t n, float *X, uint32_t ldx, float scale, cudaStream_t st);
@@ -251,11 +258,11 @@ int mlp_fp32_forward(tang_ctx *ctx, const DeviceModel &m, const tang_header *h, 
 int tc_prepare_model(tang_ctx *ctx, DeviceModel &m);
 int tc_launch(tang_ctx *ctx, Ruleset &rs, const tang_header *h, uint32_t n, uint32_t *ids, float *logits,
               int32_t *tuple, int precision, bool fused_search, DevStats *stats, cudaStream_t st,
-              const TuneEntry *tune, int variant);
+              const TuneEntry *tune, int variant, bool paper = false);
 int tc2_prepare_model(tang_ctx *ctx, DeviceModel &m);
 int tc256_prepare_model(tang_ctx *ctx, DeviceModel &m);
 
-// trainer.cu
+// trainer.cu; init != nullptr starts from that model's parameters (incremental training)
 int train_run(tang_ctx *ctx, Ruleset &rs, const tang_header *samples, uint32_t n, const tang_train_cfg &cfg,
-              std::vector<uint8_t> &blob, tang_train_report *rep);
+              std::vector<uint8_t> &blob, tang_train_report *rep, const DeviceModel *init = nullptr);
 }  // namespace tang

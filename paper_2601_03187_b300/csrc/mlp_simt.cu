@@ -1,4 +1,4 @@
-// FP32 CUDA-core kernels: the §5.2 feature encoder, a tiled SGEMM with a fused epilogue (the
+// FP32 CUDA-core kernels: the §6.2 feature encoder, a tiled SGEMM with a fused epilogue (the
 // plain one-kernel-per-stage network path and the trainer's forward/backward), argmax,
 // column sums, softmax cross-entropy and Adam.
 #include <algorithm>
@@ -7,7 +7,7 @@
 
 namespace tang {
 
-// §5.2: SIP hi/lo, DIP hi/lo, SP, DP, PRO as floats (exact), times `scale`; column 7 = 0.
+// §6.2: SIP hi/lo, DIP hi/lo, SP, DP, PRO as floats (exact), times `scale`; column 7 = 0.
 __global__ void k_encode(const tang_header *__restrict__ h, uint32_t n, float *__restrict__ X, uint32_t ldx,
                          float scale) {
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {

@@ -1,6 +1,6 @@
 // Fused classification kernel on the 5th-generation tensor cores (tcgen05, sm_103a):
-// header load + §5.2 encoding + the residual MLP of §5.1 (BF16 or FP8 operands, FP32
-// accumulation in tensor memory) + argmax + the exact tuple-space search of §4.1.1, one
+// header load + §6.2 encoding + the residual MLP of §6.1 (BF16 or FP8 operands, FP32
+// accumulation in tensor memory) + argmax + the exact tuple-space search of §5.1.1, one
 // persistent CTA per SM, one 128-packet tile at a time.
 //
 // Data flow of one tile (M = 128 packets):
@@ -273,7 +273,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
         uint32_t acc_cnt = 0, tcnt = 0;
         bool ok = true;
         // store 32 activations of row r (columns col0 .. col0+31 of the 512-wide layer input)
-        // into the swizzled shared-memory operand (u of §5.1 Eq. 1)
+        // into the swizzled shared-memory operand (u of §6.1 Eq. 1)
         auto store_smem = [&](const uint32_t *w, int col0) {
             if (!F8) {
                 const int kb = col0 >> 6, j0 = (col0 & 63) >> 3;  // 16-byte chunk index in the row
@@ -521,7 +521,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
                 if (tile < p.n_tiles && i < p.n) {
                     const Hdr h = load_header(p.headers + i);
                     Best best;
-                    const bool hit = search_packet(tb, tuples, order, h, pred, best, cn);
+                    const bool hit = search_packet(tb, tuples, order, h, pred, best, cn, (p.fused_search & 2) != 0);
                     p.ids[i] = best.id;
                     if (p.stats) {
                         st_pk++;
@@ -761,7 +761,7 @@ constexpr int kDefaultVariant = 5;  // N=256 kernel (mlp_tc256.cu)
 
 int tc_launch(tang_ctx *ctx, Ruleset &rs, const tang_header *h, uint32_t n, uint32_t *ids, float *logits,
               int32_t *tuple, int precision, bool fused_search, DevStats *stats, cudaStream_t st,
-              const TuneEntry *tune, int variant) {
+              const TuneEntry *tune, int variant, bool paper) {
     if (n == 0) return TANG_OK;
     DeviceModel &m = *rs.model;
     const bool f8 = precision == TANG_FP8;
@@ -785,7 +785,7 @@ int tc_launch(tang_ctx *ctx, Ruleset &rs, const tang_header *h, uint32_t n, uint
     prm.fold8 = f8 ? m.d_fold8 : nullptr;
     prm.C = m.C;
     prm.Cpad = m.Cpad;
-    prm.fused_search = fused_search && ids ? 1 : 0;
+    prm.fused_search = fused_search && ids ? (paper ? 3 : 1) : 0;
     prm.trace = nullptr;
 #ifdef TANG_TC_TRACE
     static unsigned long long *d_trace = nullptr;

@@ -478,7 +478,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(tc2::kThreads, 1)
                 if (i < p.n) {
                     const Hdr h = load_header(p.headers + i);
                     Best best;
-                    const bool hit = search_packet(tb, tuples, order, h, pred, best, cn);
+                    const bool hit = search_packet(tb, tuples, order, h, pred, best, cn, (p.fused_search & 2) != 0);
                     p.ids[i] = best.id;
                     if (p.stats) {
                         st_pk++;

@@ -12,7 +12,7 @@
 // Per tile (128 packets): layer 0 on the tensor core -> x (TMEM); per block: FC1 in two
 // 256-column chunks (A = x from TMEM) -> u (swizzled shared memory); FC2 in two chunks (A = u
 // from shared memory) -> x = ReLU(acc + b2 + x) in place (Eq. 1); output FC (N = Cpad) + argmax;
-// the exact search of §4.1.1 on 2 search warps.
+// the exact search of §5.1.1 on 2 search warps.
 //
 // Layer 0 (7 header fields -> 512, FP32 in the other kernels) is one K=48 BF16 contraction per
 // 256 columns with FP32 accumulation: every 16-bit field f splits exactly into bytes,
@@ -618,7 +618,7 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
                     // headers and ids stream through L2 with evict-first hints, the tables stay
                     const Hdr h = load_header_stream(p.headers + i);
                     Best best;
-                    const bool hit = search_packet(tb, tb.tuples, tb.order, h, pred, best, cn);
+                    const bool hit = search_packet(tb, tb.tuples, tb.order, h, pred, best, cn, (p.fused_search & 2) != 0);
                     __stcs(p.ids + i, best.id);
                     if (p.stats) {
                         st_pk++;

@@ -1,4 +1,4 @@
-// Device functions of the exact tuple-space search (stage 2 of §4.1.1), shared by the staged
+// Device functions of the exact tuple-space search (stage 2 of §5.1.1), shared by the staged
 // search kernel (search.cu) and the fused classification kernel (mlp_tc.cu).
 #pragma once
 
@@ -62,7 +62,7 @@ struct Counters {
     uint32_t probes, rule_reads, slot_reads;
 };
 
-// Probe tuple t with the header truncated to the tuple's lengths (§3.3); scan the run under
+// Probe tuple t with the header truncated to the tuple's lengths (§4.3); scan the run under
 // that key in (priority, id) order and stop at the first match or at the first rule that does
 // not beat the current best. Returns true if `best` improved.
 __device__ __forceinline__ bool probe_tuple(const Tables &tb, const TupleDesc &d, uint32_t t, const Hdr &h,
@@ -91,14 +91,18 @@ __device__ __forceinline__ bool probe_tuple(const Tables &tb, const TupleDesc &d
 
 // Full exact search of one header. `tuples` / `order` may point to shared-memory copies.
 // pred outside [0, T) means "no prediction". Returns true if the predicted tuple held a match.
+// paper: the post-verification exactly as §5.1.1 states it, kept for measurement: a match in the
+// predicted tuple is returned without the conflict-set probes (so it may be a lower-priority rule,
+// the uncorrected case of §5.1.1 and §8); a miss still searches the remaining tuples in order.
 __device__ __forceinline__ bool search_packet(const Tables &tb, const TupleDesc *tuples, const uint16_t *order,
-                                              const Hdr &h, int pred, Best &best, Counters &c) {
+                                              const Hdr &h, int pred, Best &best, Counters &c, bool paper = false) {
     const uint32_t T = tb.T;
     best = Best{0xFFFFFFFFu, 0xFFFFFFFFu, kEmpty, 0u, 0u};
     bool hit = false;
     if (uint32_t(pred) < T) {
         c.probes++;
         hit = probe_tuple(tb, tuples[pred], uint32_t(pred), h, best, c);
+        if (hit && paper) return true;
     }
     // After a hit r: only tuples in conflict(r) can hold a better match. After a miss: all.
     uint32_t cf0 = 0xFFFFFFFFu;

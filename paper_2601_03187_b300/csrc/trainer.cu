@@ -1,4 +1,4 @@
-// Training of TaNG's network (§5.2) on the GPU with this library's own FP32 kernels:
+// Training of TaNG's network (§6.2) on the GPU with this library's own FP32 kernels:
 // labelling by the exact tuple-space search, class balancing by oversampling up to alpha,
 // minibatch cross-entropy + Adam with a step learning-rate schedule, and rounds with
 // alpha x 10 while the held-out accuracy stays below beta.
@@ -250,16 +250,18 @@ static tang_header inside_rule(const DRule &r, SplitMix &g) {
 }
 
 int train_run(tang_ctx *ctx, Ruleset &rs, const tang_header *samples, uint32_t n, const tang_train_cfg &cfg,
-              std::vector<uint8_t> &blob, tang_train_report *rep) {
+              std::vector<uint8_t> &blob, tang_train_report *rep, const DeviceModel *init) {
     const auto t_start = std::chrono::steady_clock::now();
     auto elapsed = [&]() { return std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count(); };
     cudaStream_t st = ctx->stream;
     const uint32_t T = uint32_t(rs.host.tuples.size());
-    const uint32_t N = cfg.N ? cfg.N : 512, blocks = cfg.blocks, B = cfg.batch ? cfg.batch : 8192;
+    // incremental training keeps the shape of the model it starts from
+    const uint32_t N = init ? init->N : (cfg.N ? cfg.N : 512), blocks = init ? init->blocks : cfg.blocks;
+    const uint32_t B = cfg.batch ? cfg.batch : 8192;
     SplitMix rng{cfg.seed * 0x9E3779B97F4A7C15ULL + 12345};
     tang_train_report R{};
 
-    // 1. Label every sample with the tuple of its exact match (§5.2 raw dataset).
+    // 1. Label every sample with the tuple of its exact match (§6.2 raw dataset).
     auto label = [&](const std::vector<tang_header> &hs, std::vector<int32_t> &out) -> int {
         out.assign(hs.size(), -1);
         if (hs.empty()) return TANG_OK;
@@ -305,10 +307,18 @@ int train_run(tang_ctx *ctx, Ruleset &rs, const tang_header *samples, uint32_t n
         (i < n_hold ? hold_y : base_y).push_back(lab[keep[i]]);
     }
 
-    // 2. The network (PyTorch-style uniform init, features prescaled by 2^-16).
+    // 2. The network (PyTorch-style uniform init, features prescaled by 2^-16), or, for incremental
+    // training (§5.2.2), the deployed model's parameters with the prescale taken back out of W0
+    // (exact: a power of two).
     Trainer tr;
     if ((rc = tr.init(ctx, N, blocks, T, B))) return rc;
-    {
+    if (init) {
+        if (init->C != T || init->S != 7 || init->host_params.size() != tr.P)
+            return set_err(ctx, TANG_EINVAL, "the loaded model does not fit this ruleset's %u tuples", T);
+        std::vector<float> p(init->host_params);
+        for (size_t i = 0; i < size_t(7) * N; ++i) p[i] *= 65536.0f;
+        CK(cudaMemcpyAsync(tr.params, p.data(), 4 * tr.P, cudaMemcpyHostToDevice, st));
+    } else {
         std::vector<float> p(tr.P);
         Views v = make_views(p.data(), 7, N, blocks, T);
         auto fill = [&](float *w, size_t cnt, uint32_t fan_in) {
@@ -380,7 +390,7 @@ int train_run(tang_ctx *ctx, Ruleset &rs, const tang_header *samples, uint32_t n
     double acc = 0.0;
     float last_loss = 0.f;
     for (uint32_t round = 0; round < std::max(1u, cfg.max_rounds) && !out_of_time; ++round) {
-        // 3. §5.2 class balance: every class below alpha is oversampled up to alpha.
+        // 3. §6.2 class balance: every class below alpha is oversampled up to alpha.
         std::vector<tang_header> set_h = base_h;
         std::vector<int32_t> set_y = base_y;
         std::vector<std::vector<uint32_t>> by_class(T);

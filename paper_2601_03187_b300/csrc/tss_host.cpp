@@ -1,5 +1,5 @@
-// Host side of the tuple space: construction (§3.3), device upload, and the immediate-update
-// path (§4.2.1: delete, and insertion restricted to existing tuples).
+// Host side of the tuple space: construction (§4.3), device upload, and the immediate-update
+// path (§5.2.1: delete, and insertion restricted to existing tuples).
 //
 // The host keeps a mirror of the device tables (tuples, slots, rule pool without the conflict
 // words) so that inserts and deletes are decided on the host and applied to the device with a
@@ -109,7 +109,7 @@ int tss_build(tang_ctx *ctx, Ruleset &rs, const tang_rule *rules, uint32_t n) {
         for (uint32_t i = 1; i < n; ++i)
             if (ids[i] == ids[i - 1]) return set_err(ctx, TANG_EEXIST, "duplicate rule id %u", ids[i]);
     }
-    // Tuples in order of first appearance over the priority order (§3.3, Table 1 numbering).
+    // Tuples in order of first appearance over the priority order (§4.3, Table 1 numbering).
     std::memset(H.tuple_of_len, 0xFF, sizeof(H.tuple_of_len));
     H.tuples.clear();
     auto add_tuple = [&](uint32_t ls, uint32_t ld) {
@@ -293,8 +293,67 @@ void tss_free(tang_ctx *ctx, Ruleset &rs) {
     rs.d_desc = nullptr;
 }
 
+// Full rebuild of the tuple space over the live rules (the TSS step of §5.2.2's full retraining):
+// tuples are recomputed from the rules' own lengths, so rules that restricted insertion placed in
+// a coarser tuple move to their exact one, tuples may appear or disappear, and the counter of such
+// rules restarts at zero. The ruleset keeps its device descriptor (kernels and captured graphs
+// reach the tables through it); only the arrays it points to are replaced. same_tuples reports
+// whether the new tuple list (lengths in index order) equals the old one.
+int tss_rebuild(tang_ctx *ctx, Ruleset &rs, bool &same_tuples) {
+    const HostTSS &H = rs.host;
+    std::vector<tang_rule> live;
+    live.reserve(H.live);
+    for (const auto &kv : H.pos_of_id) {
+        const DRule &d = H.pool[kv.second];
+        tang_rule r{};
+        r.sip = d.sip;
+        r.dip = d.dip;
+        r.sp_lo = uint16_t(d.sp & 0xFFFFu);
+        r.sp_hi = uint16_t(d.sp >> 16);
+        r.dp_lo = uint16_t(d.dp & 0xFFFFu);
+        r.dp_hi = uint16_t(d.dp >> 16);
+        r.sip_len = uint8_t(meta_sip_len(d.meta));
+        r.dip_len = uint8_t(meta_dip_len(d.meta));
+        r.proto_wild = meta_proto_exact(d.meta) ? 0 : 1;
+        r.proto = uint8_t(meta_proto(d.meta));
+        r.priority = d.prio;
+        r.id = d.id;
+        live.push_back(r);
+    }
+    Ruleset fresh;
+    int rc = tss_build(ctx, fresh, live.data(), uint32_t(live.size()));
+    if (!rc) rc = tss_upload(ctx, fresh, ctx->stream);
+    if (rc) {
+        tss_free(ctx, fresh);
+        return rc;
+    }
+    same_tuples = fresh.host.tuples.size() == H.tuples.size();
+    for (size_t t = 0; same_tuples && t < H.tuples.size(); ++t)
+        same_tuples = fresh.host.tuples[t].ls == H.tuples[t].ls && fresh.host.tuples[t].ld == H.tuples[t].ld;
+    // no kernel may still read the old arrays
+    CKR(cudaDeviceSynchronize());
+    Tables *desc = rs.d_desc;
+    rs.d_desc = nullptr;
+    tss_free(ctx, rs);
+    rs.host = std::move(fresh.host);
+    rs.d_tuples = fresh.d_tuples;
+    rs.d_slots = fresh.d_slots;
+    rs.d_rules = fresh.d_rules;
+    rs.d_cwords = fresh.d_cwords;
+    rs.d_order = fresh.d_order;
+    rs.slot_capacity = fresh.slot_capacity;
+    rs.rule_capacity = fresh.rule_capacity;
+    rs.cword_capacity = fresh.cword_capacity;
+    rs.cword_rows = fresh.cword_rows;
+    ctx_free(ctx, fresh.d_desc);
+    rs.d_desc = desc;
+    if ((rc = upload_desc(ctx, rs, ctx->stream))) return rc;
+    CKR(cudaStreamSynchronize(ctx->stream));
+    return TANG_OK;
+}
+
 // ---------------------------------------------------------------------------------------
-// Immediate update (§4.2.1)
+// Immediate update (§5.2.1)
 // ---------------------------------------------------------------------------------------
 
 // Grow a device array to hold at least `need` elements (copying `used` of them). The tables'
@@ -363,7 +422,7 @@ int tss_insert(tang_ctx *ctx, Ruleset &rs, const tang_rule &r, cudaStream_t st) 
     int rc = validate_rule(ctx, r);
     if (rc) return rc;
     if (H.pos_of_id.count(r.id)) return set_err(ctx, TANG_EEXIST, "rule id %u is already live", r.id);
-    // §4.2.1: exact lengths, else the first tuple of maximal length sum with l^T <= l^R.
+    // §5.2.1: exact lengths, else the first tuple of maximal length sum with l^T <= l^R.
     int t = H.tuple_of_len[r.sip_len][r.dip_len];
     if (t < 0) {
         int best_sum = -1;

@@ -1,4 +1,4 @@
-"""GPU parity of the network (§5.1) against the float64 oracle forward, per precision and path."""
+"""GPU parity of the network (§6.1) against the float64 oracle forward, per precision and path."""
 import numpy as np
 import pytest
 import torch

@@ -165,7 +165,7 @@ def test_graph_replay_and_host_pipeline(ctx):
 
 
 def test_updates_stay_exact(ctx):
-    """Immediate update (§4.2.1): inserts and deletes; every epoch is re-checked against the oracle."""
+    """Immediate update (§5.2.1): inserts and deletes; every epoch is re-checked against the oracle."""
     rules = wl.rules_for_config(0, n_rules=3000)
     rs = ctx.load_ruleset(rules)
     tuples, _ = tss.build_tuples(rules)

@@ -1,4 +1,4 @@
-"""Pins for the oracle's float64 MLP (§5.1, Eq. 1-2), its gradients and training math (§5.2)."""
+"""Pins for the oracle's float64 MLP (§6.1, Eq. 1-2), its gradients and training math (§6.2)."""
 import numpy as np
 import pytest
 import torch
@@ -17,7 +17,7 @@ def rand_params(rng, S=7, N=8, k=2, C=5, scale=0.5):
 
 
 def test_features_segments():
-    """§5.2: SIP hi/lo, DIP hi/lo, SP, DP, PRO as 16-bit segment values."""
+    """§6.2: SIP hi/lo, DIP hi/lo, SP, DP, PRO as 16-bit segment values."""
     h = np.zeros(2, dtype=wl.HEADER_DTYPE)
     h[0] = (0x12345678, 0x9ABCDEF0, 80, 65535, 17, (0, 0, 0))
     h[1] = (0xFFFFFFFF, 0, 0, 1, 255, (0, 0, 0))

@@ -34,7 +34,7 @@ def test_table1_map_matches_set_expansion():
 
 
 def test_table1_paper_point():
-    """§3.2: the area R1 shares with R6 and R8 belongs to R1."""
+    """§4.2: the area R1 shares with R6 and R8 belongs to R1."""
     rules, names, *_ = table1()
     ex = [e for e in worked_examples() if e[0] == "classify"]
     assert ex

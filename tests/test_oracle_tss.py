@@ -1,4 +1,4 @@
-"""Pins for the oracle's tuple space (§3.3), restricted insertion (§4.2.1) and conflict sets."""
+"""Pins for the oracle's tuple space (§4.3), restricted insertion (§5.2.1) and conflict sets."""
 import itertools
 
 import numpy as np
@@ -53,7 +53,7 @@ def test_worked_examples():
             assert cands == expected.split(","), src
             assert "T4" not in cands  # (0,3) is not <= (3,1): the stated rule excludes it
         seen.add(kind)
-    assert seen == {"truncate", "insert", "candidates", "classify"}
+    assert seen == {"truncate", "insert", "candidates", "classify", "paper"}
 
 
 def test_insert_without_candidate_and_ties():

@@ -11,6 +11,7 @@ from .synth import (  # noqa: F401
     LEN_WEIGHTS_DEFAULT,
     LEN_WEIGHTS_SKEWED,
     gen_rules,
+    gen_clustered_rules,
     sample_inside,
     uniform_headers,
     zipf_ranks,

@@ -88,6 +88,56 @@ def gen_rules(
     return r
 
 
+def gen_clustered_rules(
+    n: int,
+    seed: int,
+    n_blocks: int = 64,
+    p_block_len: float = 0.97,
+    first_id: int = 0,
+    priority_range: int | None = None,
+) -> np.ndarray:
+    """Rules clustered in address blocks, each block with its own typical prefix lengths.
+
+    n_blocks distinct (SIP /8, DIP /8) pairs are drawn; every block gets a (SIP length, DIP
+    length) pair uniform over {8,16,24,32}^2. A rule picks a block uniformly, takes the block's
+    lengths with probability p_block_len (else uniform lengths from the same set), and random
+    address bits below the block's /8. Ports and protocol as gen_rules' defaults. Priorities are
+    uniform draws from [0, priority_range) (default: a permutation of 0..n-1); ids are
+    first_id + index. This stands in for rulesets whose address structure ties regions of the
+    header space to tuples (as ClassBench-ng rulesets do), which a network can learn; rules of
+    "another ruleset" are the same draw with another seed.
+    """
+    rng = np.random.default_rng(seed)
+    pairs = rng.choice(1 << 16, n_blocks, replace=False)
+    b_sip = (pairs >> 8).astype(np.uint32) << np.uint32(24)
+    b_dip = (pairs & 0xFF).astype(np.uint32) << np.uint32(24)
+    lens = np.array([8, 16, 24, 32], dtype=np.int64)
+    b_ls = rng.choice(lens, n_blocks)
+    b_ld = rng.choice(lens, n_blocks)
+    blk = rng.integers(0, n_blocks, n)
+    own = rng.random(n) < p_block_len
+    sl = np.where(own, b_ls[blk], rng.choice(lens, n))
+    dl = np.where(own, b_ld[blk], rng.choice(lens, n))
+    r = np.zeros(n, dtype=RULE_DTYPE)
+    r["sip_len"] = sl
+    r["dip_len"] = dl
+    low_s = rng.integers(0, 1 << 24, n, dtype=np.uint64).astype(np.uint32)
+    low_d = rng.integers(0, 1 << 24, n, dtype=np.uint64).astype(np.uint32)
+    r["sip"] = (b_sip[blk] | low_s) & _prefix_bits(sl)
+    r["dip"] = (b_dip[blk] | low_d) & _prefix_bits(dl)
+    r["sp_lo"], r["sp_hi"] = _ports(rng, n, 0.5, 0.3)
+    r["dp_lo"], r["dp_hi"] = _ports(rng, n, 0.5, 0.3)
+    wild = rng.random(n) < 0.5
+    r["proto_wild"] = wild.astype(np.uint8)
+    r["proto"] = np.where(wild, 0, rng.choice(PROTO_CHOICES, size=n))
+    if priority_range is None:
+        r["priority"] = rng.permutation(n).astype(np.uint32)
+    else:
+        r["priority"] = rng.integers(0, max(1, priority_range), n).astype(np.uint32)
+    r["id"] = np.arange(first_id, first_id + n, dtype=np.uint64).astype(np.uint32)
+    return r
+
+
 def sample_inside(rules: np.ndarray, idx: np.ndarray, rng: np.random.Generator) -> np.ndarray:
     """One header drawn uniformly inside each rule `rules[idx[i]]` (wildcard protocol -> 0..255)."""
     sel = rules[idx]
