@@ -394,6 +394,54 @@ def measure_deferred_update(tg, ctx, n_rules=65536, windows=10, per_window=2000,
             "runs": runs}
 
 
+def measure_model_sizes(tg, ctx, n_rules=65536, train_s=6.0, n_eval=1 << 22):
+    """Model size against accuracy and speed (§6.1 weighs the network's capacity against its
+    inference cost). One clustered ruleset (as in the dynamic experiment: a learnable mapping),
+    the same training time for every shape, then per shape: held-out accuracy, the network's
+    tuple accuracy and the paper-mode classification accuracy (the "Classi. Accu." of Tables 2-3)
+    on a separate trace, the exact search's probes per packet, and the exact classification
+    throughput on the tensor-core kernel (width 512; depth from 1 to 6 residual blocks) or, for
+    narrower networks, which only the FP32 path serves, on that path."""
+    import torch
+    rules = wl.gen_clustered_rules(n_rules, 70)
+    rs = ctx.load_ruleset(rules)
+    train_h = wl.gen_trace(rules, [("inside", 1 << 19)], 71)
+    ev = wl.gen_trace(rules, [("inside", n_eval)], 72)
+    d = torch.from_numpy(ev.view(np.uint8).reshape(-1, 16)).cuda()
+    ids = torch.empty(len(ev), dtype=torch.int32, device="cuda")
+    exact = torch.empty(len(ev), dtype=torch.int32, device="cuda")
+    ctx.classify(rs, d, exact, path="no_nn")
+    rows = []
+    for width, blocks in ((512, 1), (512, 2), (512, 3), (512, 6), (256, 2), (128, 2)):
+        blob, rep = ctx.train(rs, train_h, N=width, blocks=blocks, batch=8192, epochs=1000, max_rounds=1, alpha=100,
+                              holdout=0.05, time_budget_s=train_s, seed=73)
+        ctx.load_model(rs, blob)
+        path = "fused_bf16" if width == 512 else "plain_fp32"
+        st = ctx.classify(rs, d, ids, path=path, stats=True)
+        ctx.classify(rs, d, ids, path=path, paper=True)
+        paper_acc = float((ids == exact).float().mean().item())
+        reps = 5 if width == 512 else 1
+        for _ in range(2):
+            ctx.classify(rs, d, ids, path=path, graph=True)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            ctx.classify(rs, d, ids, path=path, graph=True)
+        e1.record()
+        e1.synchronize()
+        mpkts = reps * len(ev) / (e0.elapsed_time(e1) / 1e3) / 1e6
+        flops = 2 * 7 * width + blocks * 2 * 2 * width * width + 2 * width * ctx.ruleset_info(rs)["n_tuples"]
+        rows.append({"width": width, "blocks": blocks, "path": path, "mflop_per_pkt": round(flops / 1e6, 3),
+                     "epochs": rep["epochs_run"], "holdout_accuracy": round(rep["holdout_accuracy"], 4),
+                     "nn_accuracy": round(st["nn_correct"] / max(1, st["matched"]), 4),
+                     "paper_classification_accuracy": round(paper_acc, 5),
+                     "exact_probes_per_pkt": round(st["probes"] / len(ev), 3), "mpkts": round(mpkts, 1)})
+    ctx.unload_ruleset(rs)
+    return {"rules": n_rules, "ruleset": "clustered (64 address blocks)", "train_s_each": train_s,
+            "eval_packets": len(ev), "shapes": rows}
+
+
 def measure_peaks():
     """Denominators the driver's peak file lacks, measured with library GEMMs (cuBLAS SGEMM with
     TF32 off for FP32 SIMT; cuBLASLt E4M3 GEMM for FP8), best of a few 8192^3 runs."""
@@ -660,6 +708,7 @@ def main():
         extra["updates"] = measure_updates(tg, ctx)
         if not args.no_du:
             extra["deferred_update"] = measure_deferred_update(tg, ctx)
+            extra["model_sizes"] = measure_model_sizes(tg, ctx)
 
     # ---- e2e: host (pinned) buffers through the C ABI, copies inside the timed region
     ph = torch.empty(n * 16, dtype=torch.uint8, pin_memory=True).numpy()

@@ -156,7 +156,9 @@ typedef struct tang_model_header {
 
 /* Validate and upload a model for ruleset `rs`; keeps an FP32 copy and derives the BF16 and
  * (if calibrated) FP8 copies. Requires C == n_tuples, S == 7. The tensor-core paths further
- * require N == 512 (other N use the FP32 path only) and C <= 256.
+ * require N == 512, 1 <= blocks <= 31 and C <= 128 (other shapes use the FP32 path only); the
+ * N=128 variants (TANG_FUSED_1SM, _2SM, _MCAST2/4) serve only blocks == 6, other block counts
+ * always run the N=256 kernel.
  * Replaces a previous model of the ruleset. Synchronous: waits for all work on the device.
  * Hot swap (§5.2.2 deploys retrained weights while classification goes on): when the previous
  * model has the same S, N, blocks, C and FP8 calibration state, the new weights are written into
@@ -254,7 +256,7 @@ int tang_graph_count(tang_ctx *ctx, uint32_t *count);
  * the process exits. It calls no cudaMalloc, cudaFree or allocating library routine.
  * The paper has no counterpart; it is an addition of this library.
  *   d_headers: n device headers, 16-byte aligned; d_ids: n device outputs (same ids as
- *   tang_classify). Requires a loaded model with a tensor-core copy (N == 512, 6 blocks).
+ *   tang_classify). Requires a loaded model with a tensor-core copy (see tang_load_model).
  *   The first call on a device looks up the array's device address (cudaGetSymbolAddress),
  *   so make that first call before any stream capture that should contain later calls.
  *   All calls share the one array: calls whose kernels overlap on the GPU (on different

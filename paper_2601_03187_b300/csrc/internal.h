@@ -113,6 +113,7 @@ struct HostTSS {
 // ---------------------------------------------------------------------------------------
 struct DeviceModel {
     uint32_t S = 0, N = 0, blocks = 0, C = 0, Cpad = 0;
+    uint32_t layers = 0;              // N x N layers of the tensor-core copies (2 x blocks; 0 = none)
     std::vector<float> host_params;   // blob parameter order
     float *d_params = nullptr;        // same order, FP32 (plain path and layer 0 of every path)
     // FP32 pointers into d_params

@@ -599,16 +599,20 @@ int make_tmap(tang_ctx *ctx, CUtensorMap *m, void *base, uint32_t rows, bool f8,
 // per-output-channel scales, FP32 biases, FP8 dequantisation factors and activation scales.
 int tc_prepare_model(tang_ctx *ctx, DeviceModel &m) {
     const uint32_t N = m.N, C = m.C;
-    if (N != 512 || m.blocks != 6) return TANG_OK;  // the fused kernel is built for the paper's 6 x 512 network
+    // the tensor-core kernels are built for N = 512; the N=256 kernel takes any block count up to
+    // 31 (the N=128 variants only the paper's 6)
+    if (N != 512 || m.blocks < 1 || m.blocks > 31) return TANG_OK;
     if (C > 128) return TANG_OK;
+    const int nl = int(2 * m.blocks);  // N x N layers
+    m.layers = uint32_t(nl);
     const uint32_t Cpad = m.Cpad;  // multiple of 16
-    const size_t hid = size_t(tc::kLayers) * N * N;
+    const size_t hid = size_t(nl) * N * N;
     const size_t rows_out = Cpad;
     const float *hp = m.host_params.data();
     // host views of the FP32 parameters
     const float *W0 = hp;
     const float *p = hp + size_t(7) * N + N;
-    std::vector<const float *> W(tc::kLayers), B(tc::kLayers);
+    std::vector<const float *> W(nl), B(nl);
     for (uint32_t b = 0; b < m.blocks; ++b) {
         W[2 * b] = p;
         p += size_t(N) * N;
@@ -623,8 +627,8 @@ int tc_prepare_model(tang_ctx *ctx, DeviceModel &m) {
     const float *bc = p + size_t(N) * C;
     (void)W0;
     std::vector<__nv_bfloat16> wb(hid + rows_out * N);
-    std::vector<float> bias(size_t(tc::kLayers) * N + Cpad, 0.f);
-    for (int l = 0; l < tc::kLayers; ++l) {
+    std::vector<float> bias(size_t(nl) * N + Cpad, 0.f);
+    for (int l = 0; l < nl; ++l) {
         for (uint32_t n = 0; n < N; ++n)
             for (uint32_t k = 0; k < N; ++k) wb[size_t(l) * N * N + size_t(n) * N + k] = __float2bfloat16_rn(W[l][size_t(k) * N + n]);
         for (uint32_t n = 0; n < N; ++n) bias[size_t(l) * N + n] = B[l][n];
@@ -632,7 +636,7 @@ int tc_prepare_model(tang_ctx *ctx, DeviceModel &m) {
     for (uint32_t c = 0; c < Cpad; ++c)
         for (uint32_t k = 0; k < N; ++k)
             wb[hid + size_t(c) * N + k] = __float2bfloat16_rn(c < C ? Wc[size_t(k) * C + c] : 0.f);
-    for (uint32_t c = 0; c < C; ++c) bias[size_t(tc::kLayers) * N + c] = bc[c];
+    for (uint32_t c = 0; c < C; ++c) bias[size_t(nl) * N + c] = bc[c];
     int rc = ctx_alloc(ctx, wb.size() * 2, &m.d_wbf16);
     if (!rc) rc = ctx_alloc(ctx, bias.size() * 4, (void **)&m.d_bias_tc);
     if (rc) return rc;
@@ -644,19 +648,19 @@ int tc_prepare_model(tang_ctx *ctx, DeviceModel &m) {
     m.tmap_bf16 = maps;
     for (int ci = 0; ci < 3; ++ci) {
         const uint32_t cs = 1u << ci;
-        if ((rc = make_tmap(ctx, &maps[ci].hid, m.d_wbf16, tc::kLayers * N, false, 128 / cs))) return rc;
+        if ((rc = make_tmap(ctx, &maps[ci].hid, m.d_wbf16, nl * N, false, 128 / cs))) return rc;
         if ((rc = make_tmap(ctx, &maps[ci].out, static_cast<__nv_bfloat16 *>(m.d_wbf16) + hid, Cpad, false, Cpad / cs)))
             return rc;
     }
 
     if (m.has_fp8) {
         // activation scale: the power of two that maps the calibrated max |x| into (224, 448]
-        for (int j = 0; j <= tc::kLayers; ++j) {
+        for (int j = 0; j <= nl; ++j) {
             const float amax = m.act_amax[j];
             m.act_scale[j] = std::ldexp(1.0f, int(std::floor(std::log2(448.0 / double(amax)))));
         }
         std::vector<uint8_t> w8(hid + rows_out * N, 0);
-        std::vector<float> dq(size_t(tc::kLayers) * N + Cpad, 0.f);
+        std::vector<float> dq(size_t(nl) * N + Cpad, 0.f);
         auto quant_col = [&](const float *Wsrc, uint32_t ncols, uint32_t n, size_t dst_row, float sa, float *dq_out) {
             float amax = 0.f;
             for (uint32_t k = 0; k < N; ++k) amax = std::max(amax, std::fabs(Wsrc[size_t(k) * ncols + n]));
@@ -665,25 +669,25 @@ int tc_prepare_model(tang_ctx *ctx, DeviceModel &m) {
                 w8[dst_row * N + k] = __nv_cvt_float_to_fp8(Wsrc[size_t(k) * ncols + n] * sw, __NV_SATFINITE, __NV_E4M3);
             *dq_out = 1.0f / (sa * sw);
         };
-        for (int l = 0; l < tc::kLayers; ++l)
+        for (int l = 0; l < nl; ++l)
             for (uint32_t n = 0; n < N; ++n)
                 quant_col(W[l], N, n, size_t(l) * N + n, m.act_scale[l], &dq[size_t(l) * N + n]);
         for (uint32_t c = 0; c < C; ++c)
-            quant_col(Wc, C, c, hid / N + c, m.act_scale[tc::kLayers], &dq[size_t(tc::kLayers) * N + c]);
+            quant_col(Wc, C, c, hid / N + c, m.act_scale[nl], &dq[size_t(nl) * N + c]);
         rc = ctx_alloc(ctx, w8.size(), &m.d_wfp8);
-        if (!rc) rc = ctx_alloc(ctx, (dq.size() + 16) * 4, (void **)&m.d_wscale8);
+        if (!rc) rc = ctx_alloc(ctx, (dq.size() + nl + 1) * 4, (void **)&m.d_wscale8);
         if (rc) return rc;
         cudaMemcpy(m.d_wfp8, w8.data(), w8.size(), cudaMemcpyHostToDevice);
         cudaMemcpy(m.d_wscale8, dq.data(), dq.size() * 4, cudaMemcpyHostToDevice);
-        // the 13 activation scales follow the dequantisation factors
-        cudaMemcpy(m.d_wscale8 + dq.size(), m.act_scale, 13 * 4, cudaMemcpyHostToDevice);
+        // the nl + 1 activation scales follow the dequantisation factors
+        cudaMemcpy(m.d_wscale8 + dq.size(), m.act_scale, (nl + 1) * 4, cudaMemcpyHostToDevice);
         // the output scale s[l+1] folded into each hidden layer's dequantisation factor and bias;
         // s is a power of two, so relu(s * (acc * dq + b)) is bit-identical to the unfolded form
-        std::vector<float> fold(size_t(2) * tc::kLayers * N);
-        for (int l = 0; l < tc::kLayers; ++l)
+        std::vector<float> fold(size_t(2) * nl * N);
+        for (int l = 0; l < nl; ++l)
             for (uint32_t n = 0; n < N; ++n) {
                 fold[size_t(l) * N + n] = dq[size_t(l) * N + n] * m.act_scale[l + 1];
-                fold[size_t(tc::kLayers + l) * N + n] = bias[size_t(l) * N + n] * m.act_scale[l + 1];
+                fold[size_t(nl + l) * N + n] = bias[size_t(l) * N + n] * m.act_scale[l + 1];
             }
         if ((rc = ctx_alloc(ctx, fold.size() * 4, (void **)&m.d_fold8))) return rc;
         cudaMemcpy(m.d_fold8, fold.data(), fold.size() * 4, cudaMemcpyHostToDevice);
@@ -691,12 +695,12 @@ int tc_prepare_model(tang_ctx *ctx, DeviceModel &m) {
         m.tmap_fp8 = m8;
         for (int ci = 0; ci < 3; ++ci) {
             const uint32_t cs = 1u << ci;
-            if ((rc = make_tmap(ctx, &m8[ci].hid, m.d_wfp8, tc::kLayers * N, true, 128 / cs))) return rc;
+            if ((rc = make_tmap(ctx, &m8[ci].hid, m.d_wfp8, nl * N, true, 128 / cs))) return rc;
             if ((rc = make_tmap(ctx, &m8[ci].out, static_cast<uint8_t *>(m.d_wfp8) + hid, Cpad, true, Cpad / cs)))
                 return rc;
         }
     }
-    if ((rc = tc2_prepare_model(ctx, m))) return rc;
+    if (nl == tc::kLayers && (rc = tc2_prepare_model(ctx, m))) return rc;
     if ((rc = tc256_prepare_model(ctx, m))) return rc;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return set_err(ctx, TANG_EDEVICE, "tc_prepare_model: %s", cudaGetErrorString(e));
@@ -781,7 +785,8 @@ int tc_launch(tang_ctx *ctx, Ruleset &rs, const tang_header *h, uint32_t n, uint
     prm.b0 = m.b0;
     prm.bias = m.d_bias_tc;
     prm.dq = f8 ? m.d_wscale8 : nullptr;
-    prm.sa = f8 ? m.d_wscale8 + size_t(tc::kLayers) * m.N + m.Cpad : nullptr;
+    prm.sa = f8 ? m.d_wscale8 + size_t(m.layers) * m.N + m.Cpad : nullptr;
+    prm.layers = m.layers;
     prm.fold8 = f8 ? m.d_fold8 : nullptr;
     prm.C = m.C;
     prm.Cpad = m.Cpad;
@@ -793,12 +798,15 @@ int tc_launch(tang_ctx *ctx, Ruleset &rs, const tang_header *h, uint32_t n, uint
     cudaMemsetAsync(d_trace, 0, sizeof(unsigned long long) * trace::kTotal, st);
     prm.trace = d_trace;
 #endif
-    const int v = variant ? variant : (tune && tune->fused_variant ? tune->fused_variant : kDefaultVariant);
+    int v = variant ? variant : (tune && tune->fused_variant ? tune->fused_variant : kDefaultVariant);
+    if (m.layers != uint32_t(tc::kLayers)) v = 5;  // the N=128 variants are built for 6 blocks
     if (v == 2 || v == 5) {
         const int rc = v == 2 ? tc2_launch(ctx, m, prm, f8, st, tune ? tune->fused_grid : 0)
                               : tc256_launch(ctx, m, prm, f8, st, tune ? tune->fused_grid : 0);
         if (rc != TANG_EUNSUPPORTED) return rc;  // models without those maps run the 1-SM N=128 kernel
     }
+    if (m.layers != uint32_t(tc::kLayers))
+        return set_err(ctx, TANG_EUNSUPPORTED, "no tensor-core kernel for a %u-block model", m.blocks);
     // variants 1, 3, 4: the 1-SM kernel with weight tiles shared by clusters of 1, 2, 4 CTAs
     const int ci = v == 3 ? 1 : v == 4 ? 2 : 0;
     int rc = ci == 0 ? (f8 ? launch_1sm<true, 1>(ctx, maps[0], prm, st, tune) : launch_1sm<false, 1>(ctx, maps[0], prm, st, tune))

@@ -12,7 +12,7 @@
 // Per tile (128 packets): layer 0 on the tensor core -> x (TMEM); per block: FC1 in two
 // 256-column chunks (A = x from TMEM) -> u (swizzled shared memory); FC2 in two chunks (A = u
 // from shared memory) -> x = ReLU(acc + b2 + x) in place (Eq. 1); output FC (N = Cpad) + argmax;
-// the exact search of §5.1.1 on 2 search warps.
+// the exact search of §5.1.1 on 4 search warps.
 //
 // Layer 0 (7 header fields -> 512, FP32 in the other kernels) is one K=48 BF16 contraction per
 // 256 columns with FP32 accumulation: every 16-bit field f splits exactly into bytes,
@@ -43,7 +43,6 @@ namespace tang {
 namespace tc256 {
 constexpr int kM = 128;
 constexpr int kHid = 512;
-constexpr int kLayers = 12;
 constexpr int kStageBytes = 32768;  // 256 rows x 128 bytes
 constexpr int kNumEpiWarps = 16;
 // Warp groups (4 warps each): 0 = producer (warp 0) and MMA issuer (warp 1); 1..4 = the epilogue;
@@ -111,6 +110,7 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
     volatile int *sAbort = reinterpret_cast<volatile int *>(smem + Lay::kOffMisc + 4);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nl = int(p.layers);  // N x N layers: 2 per residual block
     constexpr int KB = F8 ? 4 : 8;
     constexpr int KBW = F8 ? 128 : 64;
     constexpr uint32_t kActArrivals = F8 ? 8 : 4;  // 64-column units per K-block x 4 lane quadrants
@@ -184,13 +184,13 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
                     ptx::tma_load_2d(dst, &tm_l0, &full[stage], 0, c * 256);
                     advance();
                 }
-                for (int L = 0; L <= kLayers && ok; ++L) {
-                    const int nch = L == kLayers ? 1 : 2;
+                for (int L = 0; L <= nl && ok; ++L) {
+                    const int nch = L == nl ? 1 : 2;
                     for (int c = 0; c < nch && ok; ++c)
                         for (int kb = 0; kb < KB; ++kb) {
                             uint8_t *dst = next_stage();
                             if (!dst) break;
-                            if (L < kLayers) {
+                            if (L < nl) {
                                 ptx::mbar_arrive_expect_tx(&full[stage], kStageBytes);
                                 ptx::tma_load_2d(dst, &tm_hid, &full[stage], kb * KBW, L * kHid + c * 256);
                             } else {
@@ -249,10 +249,10 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
                     ptx::mma_commit(acc_full);
                     TC_TRACE(trace::kMma + uses * 12 + 10, uses < uint32_t(trace::kChunks));
                 }
-                for (int L = 0; L <= kLayers && !err; ++L, ++lay) {
+                for (int L = 0; L <= nl && !err; ++L, ++lay) {
                     const bool a_tmem = (L & 1) == 0;  // FC1 and the output layer read x from TMEM
-                    const int nch = L == kLayers ? 1 : 2;
-                    const uint32_t idesc = L == kLayers ? idesc_o : idesc_h;
+                    const int nch = L == nl ? 1 : 2;
+                    const uint32_t idesc = L == nl ? idesc_o : idesc_h;
                     for (int c = 0; c < nch && !err; ++c, ++uses) {
                         TC_TRACE(trace::kMma + uses * 12 + 0, uses < uint32_t(trace::kChunks));
                         if (!ptx::mbar_wait(acc_empty, (uses - 1) & 1, sAbort, kTimeoutNs)) {
@@ -416,10 +416,10 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
             }
             if (!ok) break;
             // ---- hidden layers, two 256-column chunks each
-            for (int L = 0; L < kLayers && ok; ++L) {
+            for (int L = 0; L < nl && ok; ++L) {
                 const bool fc2 = (L & 1) != 0;
                 // BF16: v = acc + b. FP8: v = acc * (dq * s_out) + b * s_out, in the output's units.
-                const float4 *bv = reinterpret_cast<const float4 *>(F8 ? p.fold8 + size_t(kLayers + L) * kHid
+                const float4 *bv = reinterpret_cast<const float4 *>(F8 ? p.fold8 + size_t(nl + L) * kHid
                                                                         : p.bias + size_t(L) * kHid);
                 const float4 *dv = F8 ? reinterpret_cast<const float4 *>(p.fold8 + size_t(L) * kHid) : nullptr;
                 // FP8 residual: x is stored in the units of its own layer input (scale s[L-1])
@@ -431,8 +431,8 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
                     // the next chunk's bias (and FP8 scale) lines of this warp's unit into L1
                     {
                         const int nL = c == 0 ? L : L + 1, nunit = 4 * (c ^ 1) + g;
-                        if (nL < kLayers && lane < (F8 ? 4 : 2)) {
-                            const float *src = F8 ? p.fold8 + size_t((lane & 2 ? kLayers : 0) + nL) * kHid + nunit * 64 + (lane & 1) * 32
+                        if (nL < nl && lane < (F8 ? 4 : 2)) {
+                            const float *src = F8 ? p.fold8 + size_t((lane & 2 ? nl : 0) + nL) * kHid + nunit * 64 + (lane & 1) * 32
                                                   : p.bias + size_t(nL) * kHid + nunit * 64 + lane * 32;
                             asm volatile("prefetch.global.L1 [%0];" ::"l"(src));
                         }
@@ -511,7 +511,7 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
                     TC_TRACE(tslot + 3, tr);
                     // after the last FC2 chunk (its MMAs, the last readers of u, have completed):
                     // the next tile's layer-0 operand
-                    if (L == kLayers - 1 && c == 1 && g == 0 && tile + gridDim.x < p.n_tiles) write_features(tile + gridDim.x);
+                    if (L == nl - 1 && c == 1 && g == 0 && tile + gridDim.x < p.n_tiles) write_features(tile + gridDim.x);
                 }
             }
             if (!ok) break;
@@ -529,8 +529,8 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
                 int arg = 0;
                 {
                     const uint32_t cq = p.Cpad / 4;  // a multiple of 8
-                    const float *bias = p.bias + kLayers * kHid;
-                    const float *dq = F8 ? p.dq + kLayers * kHid : nullptr;
+                    const float *bias = p.bias + nl * kHid;
+                    const float *dq = F8 ? p.dq + nl * kHid : nullptr;
                     for (uint32_t c0 = uint32_t(g) * cq; c0 < uint32_t(g + 1) * cq; c0 += 8) {
                         uint32_t a[8];
                         ptx::tmem_ld8(tmem + lane_base + c0, a);
@@ -705,12 +705,12 @@ int tc256_prepare_model(tang_ctx *ctx, DeviceModel &m) {
     cudaMemcpy(m.d_l0, l0.data(), l0.size() * 2, cudaMemcpyHostToDevice);
     const TcMaps *one = static_cast<const TcMaps *>(m.tmap_bf16);
     maps[0].out = one[0].out;
-    if ((rc = make_tmap(ctx, &maps[0].hid, m.d_wbf16, tc256::kLayers * m.N, false, 256))) return rc;
+    if ((rc = make_tmap(ctx, &maps[0].hid, m.d_wbf16, m.layers * m.N, false, 256))) return rc;
     if ((rc = make_tmap(ctx, &maps[0].l0, m.d_l0, 512, false, 256, tc256::kL0K))) return rc;
     if (m.d_wfp8) {
         const TcMaps *one8 = static_cast<const TcMaps *>(m.tmap_fp8);
         maps[1].out = one8[0].out;
-        if ((rc = make_tmap(ctx, &maps[1].hid, m.d_wfp8, tc256::kLayers * m.N, true, 256))) return rc;
+        if ((rc = make_tmap(ctx, &maps[1].hid, m.d_wfp8, m.layers * m.N, true, 256))) return rc;
         rc = make_tmap(ctx, &maps[1].l0, static_cast<__nv_bfloat16 *>(m.d_l0) + size_t(512) * tc256::kL0K, 512, false,
                        256, tc256::kL0K);
     }

@@ -24,6 +24,7 @@ struct TcParams {
     const float *sa;        // FP8 only: [13] activation scales of the layers' inputs
     const float *fold8;     // FP8 only: [12][512] dq * s_out, then [12][512] bias * s_out (N=256 kernel)
     uint32_t C, Cpad;
+    uint32_t layers;        // N x N layers (2 x residual blocks); the N=128 kernels require 12
     int fused_search;       // bit 0: run the search warps; bit 1: paper-mode post-verification
     unsigned long long *trace;  // event timestamps of CTA 0 (trace builds only, else null)
 };

@@ -139,3 +139,41 @@ def test_predictions_agree_across_precisions(setup):
     scale = np.abs(z16).max(axis=1, keepdims=True) + 1e-30
     assert np.median(np.abs(zv - z16) / scale) < 1e-3
     assert (tv == t16).mean() > 0.998
+
+
+@pytest.mark.parametrize("blocks", [1, 2, 3])
+def test_other_depths_on_the_n256_kernel(blocks):
+    """Networks of 1-3 residual blocks (the model-size sweep) run on the N=256 kernel: logits
+    within the bound of the float64 forward of the quantised weights (BF16 and FP8), rule ids
+    exact; the N=128 variants, built for 6 blocks, are not used for them."""
+    ctx = tg.Context(0)
+    rules = wl.rules_for_config(0)
+    rs = ctx.load_ruleset(rules)
+    T = ctx.ruleset_info(rs)["n_tuples"]
+    p = random_params(np.random.default_rng(100 + blocks), N=512, blocks=blocks, C=T)
+    h = wl.trace_for_config(0, rules, seed=9)[:20000 + 3]
+    X = mlp.features(h[:4096])
+    p64 = {k: ([a.astype(np.float64) for a in v] if isinstance(v, list) else v.astype(np.float64)) for k, v in p.items()}
+    _, cache = mlp.forward(p64, X, keep=True)
+    amax = []
+    for k in range(blocks):
+        amax += [np.abs(cache["h_in"][k]).max(), np.abs(cache["u"][k]).max()]
+    amax.append(np.abs(cache["h_out"]).max())
+    ctx.load_model(rs, tg.pack_model(p, np.array(amax, dtype=np.float32)))
+    for prec in ("bf16", "fp8"):
+        q = bf16_weights(p64) if prec == "bf16" else e4m3_weights(p64)
+        z64 = mlp.forward(q, X)
+        for variant in (None, "1sm"):  # "1sm" falls back to the N=256 kernel for these depths
+            z, tup = infer(ctx, rs, h[:4096], T, tg.BF16 if prec == "bf16" else tg.FP8, variant)
+            tol = logit_tolerance(q, X, U32, U_BF16 if prec == "bf16" else U_E4M3)
+            assert np.isfinite(z).all()
+            assert (np.abs(z - z64) <= tol).all(), (prec, float((np.abs(z - z64) / tol).max()))
+            assert (tup == np.argmax(z, axis=1)).all()
+    want = oc.classify(rules, h)
+    d = to_dev(h)
+    for path in ("fused_bf16", "fused_fp8", "staged_bf16", "plain_fp32"):
+        ids = ids_dev(len(h))
+        ctx.classify(rs, d, ids, path=path)
+        torch.cuda.synchronize()
+        assert (ids_host(ids) == want).all(), path
+    ctx.close()
