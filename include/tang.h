@@ -246,6 +246,28 @@ int tang_search_ex(tang_ctx *ctx, uint32_t rs, const tang_header *d_headers, con
  * ruleset's model; a same-shape model swap (tang_load_model) keeps them. */
 int tang_graph_count(tang_ctx *ctx, uint32_t *count);
 
+/* The paper's CPU-GPU hybrid streaming framework (§5.1.2, Fig. 4), as a comparison pipeline:
+ * host headers are batched; each batch is split into `streams` segments on as many CUDA streams;
+ * the GPU runs only the network on them (stage 1; predicted tuples back to pinned host memory),
+ * and `threads` host threads run the tuple-space search (stage 2) on a snapshot of the device
+ * tables taken at the start of the call, double-buffered against the GPU's next batch.
+ * The search is exact (flags 0, same ids as tang_classify) or the paper's own post-verification
+ * (TANG_SEARCH_PAPER). headers / ids are host memory; synchronous. */
+typedef struct tang_hybrid_cfg {
+    uint32_t batch;     /* packets per batch (paper: 8192; 0 = 8192) */
+    uint32_t streams;   /* CUDA streams per batch (paper: 4; 0 = 4; at most 16). FP32 runs its
+                           segments in order on one stream (its kernels share a scratch buffer) */
+    uint32_t threads;   /* host search threads (0 = all hardware threads) */
+    uint32_t precision; /* TANG_FP32, TANG_BF16 or TANG_FP8 network */
+    uint32_t flags;     /* 0 or TANG_SEARCH_PAPER */
+    uint32_t reserved[3];
+} tang_hybrid_cfg;
+/* Errors: TANG_EINVAL (no model, bad precision or flags), TANG_EUNSUPPORTED (no tensor-core copy
+ * for BF16/FP8), TANG_ENOTFOUND, TANG_ENOMEM, TANG_EDEVICE. `stats` (may be NULL) counts the
+ * host search's work as tang_classify's counters do. */
+int tang_classify_hybrid(tang_ctx *ctx, uint32_t rs, const tang_header *headers, uint32_t n, uint32_t *ids,
+                         const tang_hybrid_cfg *cfg, tang_stats *stats);
+
 /* Staged BF16 classification (the tensor-core network kernel, then the search kernel) for
  * callers that must not allocate device memory during a call: code running inside a custom
  * allocator or allocation hook, processes whose device memory is fixed at start-up, and

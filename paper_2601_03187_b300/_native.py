@@ -79,6 +79,11 @@ class DuWindow(ctypes.Structure):
                 ("suboptimal", ctypes.c_uint64), ("decision", ctypes.c_int)]
 
 
+class HybridCfg(ctypes.Structure):
+    _fields_ = [("batch", ctypes.c_uint32), ("streams", ctypes.c_uint32), ("threads", ctypes.c_uint32),
+                ("precision", ctypes.c_uint32), ("flags", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 3)]
+
+
 class ServeCfg(ctypes.Structure):
     _fields_ = [("max_inflight", ctypes.c_uint32), ("max_batch", ctypes.c_uint32), ("path", ctypes.c_uint32),
                 ("reserved", ctypes.c_uint32)]
@@ -124,6 +129,7 @@ _SIGS = {
     "tang_finetune": (_I, [_P, _U32, _P, _U32, ctypes.POINTER(TrainCfg), _P, ctypes.POINTER(_SZ), ctypes.POINTER(TrainReport)]),
     "tang_rebuild_ruleset": (_I, [_P, _U32, ctypes.POINTER(_I)]),
     "tang_du_apply": (_I, [_P, _U32, _I, _P, _U32, ctypes.POINTER(TrainCfg), ctypes.POINTER(TrainReport)]),
+    "tang_classify_hybrid": (_I, [_P, _U32, _P, _U32, _P, ctypes.POINTER(HybridCfg), ctypes.POINTER(Stats)]),
 }
 
 
@@ -344,6 +350,20 @@ class Context:
         c = ctypes.c_uint32()
         self._ck(lib.tang_graph_count(self._h, ctypes.byref(c)), "graph_count")
         return c.value
+
+    def classify_hybrid(self, rs: int, headers: np.ndarray, ids: np.ndarray, batch=8192, streams=4, threads=0,
+                        precision=BF16, paper=False, stats=False):
+        """The paper's CPU-GPU pipeline (tang_classify_hybrid): network on the GPU, search on host threads."""
+        if not isinstance(headers, np.ndarray) or headers.dtype != HEADER_DTYPE:
+            raise TypeError("host headers (HEADER_DTYPE) required")
+        if not isinstance(ids, np.ndarray) or ids.dtype != np.uint32 or len(ids) < len(headers):
+            raise TypeError("host uint32 ids of at least len(headers) required")
+        c = HybridCfg(batch=batch, streams=streams, threads=threads, precision=precision,
+                      flags=SEARCH_PAPER if paper else 0)
+        st = Stats()
+        self._ck(lib.tang_classify_hybrid(self._h, rs, headers.ctypes.data, len(headers), ids.ctypes.data,
+                                          ctypes.byref(c), ctypes.byref(st) if stats else None), "classify_hybrid")
+        return st.as_dict() if stats else None
 
     def classify_noalloc(self, rs: int, headers, ids, stream=None):
         """Staged BF16 classify whose inter-kernel scratch is a static device array (no allocation)."""
