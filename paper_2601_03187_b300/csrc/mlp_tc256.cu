@@ -390,6 +390,28 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
             if (lane == 0) ptx::mbar_arrive(feat_full);
         };
 
+        // Per-column constants of the hidden layers, one per lane: the bias (FP8: b * s_out) and,
+        // for FP8, the scale dq * s_out of columns unit * 64 + lane and unit * 64 + 32 + lane.
+        // Shuffles broadcast them across the warp's rows. They are loaded one chunk ahead: loads
+        // issued at the chunk's start stalled the FP8 epilogue, which runs behind the MMAs and so
+        // finds its accumulator ready, for an L2 round trip; broadcast loads of whole lines missed
+        // the small L1 left beside 231 KB of shared memory in both precisions (about 1k cycles per
+        // chunk); broadcast reads from a shared-memory copy were no faster than the shuffles.
+        struct ColConst {
+            float b0, b1, d0, d1;
+        };
+        auto load_cc = [&](int L, int c) -> ColConst {
+            const int col = (4 * c + g) * 64 + lane;
+            const float *bv = F8 ? p.fold8 + size_t(nl + L) * kHid : p.bias + size_t(L) * kHid;
+            ColConst r{__ldg(bv + col), __ldg(bv + col + 32), 0.f, 0.f};
+            if (F8) {
+                const float *dv = p.fold8 + size_t(L) * kHid;
+                r.d0 = __ldg(dv + col);
+                r.d1 = __ldg(dv + col + 32);
+            }
+            return r;
+        };
+        ColConst next_cc = load_cc(0, 0);
         if (g == 0) write_features(blockIdx.x);
         for (uint32_t tile = blockIdx.x; tile < p.n_tiles && ok; tile += gridDim.x) {
             const uint32_t i = tile * kM + r;
@@ -419,24 +441,16 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
             for (int L = 0; L < nl && ok; ++L) {
                 const bool fc2 = (L & 1) != 0;
                 // BF16: v = acc + b. FP8: v = acc * (dq * s_out) + b * s_out, in the output's units.
-                const float4 *bv = reinterpret_cast<const float4 *>(F8 ? p.fold8 + size_t(nl + L) * kHid
-                                                                        : p.bias + size_t(L) * kHid);
-                const float4 *dv = F8 ? reinterpret_cast<const float4 *>(p.fold8 + size_t(L) * kHid) : nullptr;
                 // FP8 residual: x is stored in the units of its own layer input (scale s[L-1])
                 const float rr = F8 && fc2 ? sa[L + 1] / sa[L - 1] : 1.f;
                 for (int c = 0; c < 2; ++c, ++uses) {
                     [[maybe_unused]] const bool tr = lane == 0 && q == 2 && g < 2 && uses < uint32_t(trace::kChunks);
                     [[maybe_unused]] const int tslot = trace::kEpi + (g * trace::kChunks + int(uses)) * 4;
                     TC_TRACE(tslot + 0, tr);
-                    // the next chunk's bias (and FP8 scale) lines of this warp's unit into L1
-                    {
-                        const int nL = c == 0 ? L : L + 1, nunit = 4 * (c ^ 1) + g;
-                        if (nL < nl && lane < (F8 ? 4 : 2)) {
-                            const float *src = F8 ? p.fold8 + size_t((lane & 2 ? nl : 0) + nL) * kHid + nunit * 64 + (lane & 1) * 32
-                                                  : p.bias + size_t(nL) * kHid + nunit * 64 + lane * 32;
-                            asm volatile("prefetch.global.L1 [%0];" ::"l"(src));
-                        }
-                    }
+                    const int unit = 4 * c + g;
+                    // this chunk's column constants, loaded one chunk ago; now the next chunk's
+                    const ColConst cc = next_cc;
+                    next_cc = load_cc(c == 0 ? L : (L + 1 < nl ? L + 1 : 0), c ^ 1);
                     if (!ptx::mbar_wait(acc_full, uses & 1, sAbort, kTimeoutNs)) {
                         fail(16);
                         ok = false;
@@ -444,7 +458,6 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
                     }
                     TC_TRACE(tslot + 1, tr);
                     ptx::tc_fence_after();
-                    const int unit = 4 * c + g;
                     uint32_t a0[32], a1[32];
                     ptx::tmem_ld32(tmem + lane_base + g * 64, a0);
                     ptx::tmem_ld32(tmem + lane_base + g * 64 + 32, a1);
@@ -458,25 +471,15 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
                     for (int s = 0; s < 2; ++s) {
                         const int col0 = unit * 64 + s * 32;
                         const uint32_t *a = s == 0 ? a0 : a1;
+                        const float bl = s == 0 ? cc.b0 : cc.b1, dl = s == 0 ? cc.d0 : cc.d1;
                         float v[32];
 #pragma unroll
-                        for (int j4 = 0; j4 < 8; ++j4) {
-                            const float4 b = __ldg(bv + col0 / 4 + j4);
-                            const float y0 = __uint_as_float(a[4 * j4]), y1 = __uint_as_float(a[4 * j4 + 1]);
-                            const float y2 = __uint_as_float(a[4 * j4 + 2]), y3 = __uint_as_float(a[4 * j4 + 3]);
-                            if (F8) {
-                                const float4 d = __ldg(dv + col0 / 4 + j4);
-                                v[4 * j4 + 0] = fmaf(y0, d.x, b.x);
-                                v[4 * j4 + 1] = fmaf(y1, d.y, b.y);
-                                v[4 * j4 + 2] = fmaf(y2, d.z, b.z);
-                                v[4 * j4 + 3] = fmaf(y3, d.w, b.w);
-                            } else {
-                                v[4 * j4 + 0] = y0 + b.x;
-                                v[4 * j4 + 1] = y1 + b.y;
-                                v[4 * j4 + 2] = y2 + b.z;
-                                v[4 * j4 + 3] = y3 + b.w;
-                            }
+                        for (int j = 0; j < 32; ++j) {
+                            const float b = __shfl_sync(0xFFFFFFFFu, bl, j);
+                            const float y = __uint_as_float(a[j]);
+                            v[j] = F8 ? fmaf(y, __shfl_sync(0xFFFFFFFFu, dl, j), b) : y + b;
                         }
+                        TC_TRACE(trace::kEpiX + (g * trace::kChunks + int(uses)) * 6 + 3 * s + 0, tr);
                         if (fc2) {
                             if (!F8) {
                                 uint32_t xr[16];
@@ -501,7 +504,9 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
                                 }
                             }
                         }
+                        TC_TRACE(trace::kEpiX + (g * trace::kChunks + int(uses)) * 6 + 3 * s + 1, tr);
                         emit(v, col0, fc2);
+                        TC_TRACE(trace::kEpiX + (g * trace::kChunks + int(uses)) * 6 + 3 * s + 2, tr);
                     }
                     if (fc2)
                         ptx::tmem_wait_st();

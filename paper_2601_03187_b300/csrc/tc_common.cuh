@@ -38,7 +38,8 @@ constexpr int kProd = kEpi + 2 * kChunks * 4;  // [load]: empty ok
 constexpr int kLoads = 800;
 constexpr int kSearch = kProd + kLoads;        // [tile][2]: search warp 0 got the tile, finished it
 constexpr int kSearchTiles = 32;
-constexpr int kTotal = kSearch + 2 * kSearchTiles;
+constexpr int kEpiX = kSearch + 2 * kSearchTiles;  // [warp 0/1][chunk][6]: per 32-column half: math, residual, stored
+constexpr int kTotal = kEpiX + 2 * kChunks * 6;
 }  // namespace trace
 #ifdef TANG_TC_TRACE
 #define TC_TRACE(slot, limit)                                                        \
