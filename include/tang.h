@@ -424,9 +424,19 @@ int tang_du_apply(tang_ctx *ctx, uint32_t rs, int decision, const tang_header *s
  * Autotuning and serving
  * ------------------------------------------------------------------------------------- */
 
-/* Time the fused kernel's launch variants (CTAs per SM, pipeline stages, search mode) on
- * `n` device headers and keep the fastest per (ruleset, path). Synchronous. */
+/* Time the launch variants of a path on `n` device headers and keep the fastest per
+ * (ruleset, path): for the fused paths the tensor-core kernel variant and its persistent CTA
+ * count, for the search-kernel paths the block size and blocks per SM. Drops captured graphs
+ * (they hold the previous launch shape). Synchronous. */
 int tang_autotune(tang_ctx *ctx, uint32_t rs, const tang_header *d_headers, uint32_t n, uint32_t flags);
+
+/* The launch shape tang_autotune chose for (rs, path): variant = the fused kernel variant
+ * (0 = library default, 1 = N=128 one SM, 2 = CTA pairs, 3 / 4 = clusters of 2 / 4, 5 = N=256),
+ * grid = persistent CTAs (0 = one per SM), search_threads / search_bps = the search kernel's
+ * block size and blocks per SM (0 = default), ms = the time per call measured for the choice
+ * (0 if the path was never tuned). Outputs may be NULL. */
+int tang_autotune_get(tang_ctx *ctx, uint32_t rs, uint32_t path, int *variant, int *grid, int *search_threads,
+                      int *search_bps, float *ms);
 
 typedef struct tang_serve_cfg {
     uint32_t max_inflight;   /* requests on the GPU at once (slots) */

@@ -130,6 +130,7 @@ _SIGS = {
     "tang_rebuild_ruleset": (_I, [_P, _U32, ctypes.POINTER(_I)]),
     "tang_du_apply": (_I, [_P, _U32, _I, _P, _U32, ctypes.POINTER(TrainCfg), ctypes.POINTER(TrainReport)]),
     "tang_classify_hybrid": (_I, [_P, _U32, _P, _U32, _P, ctypes.POINTER(HybridCfg), ctypes.POINTER(Stats)]),
+    "tang_autotune_get": (_I, [_P, _U32, _U32] + [ctypes.POINTER(_I)] * 4 + [ctypes.POINTER(_F)]),
 }
 
 
@@ -471,6 +472,15 @@ class Context:
         n = _n_headers(headers)
         flags = PATHS[path] if isinstance(path, str) else int(path)
         self._ck(lib.tang_autotune(self._h, rs, _ptr(headers), n, flags), "autotune")
+
+    def autotune_get(self, rs: int, path="fused_bf16") -> dict:
+        v = [ctypes.c_int() for _ in range(4)]
+        ms = ctypes.c_float()
+        self._ck(lib.tang_autotune_get(self._h, rs, PATHS[path] if isinstance(path, str) else int(path),
+                                       *[ctypes.byref(x) for x in v], ctypes.byref(ms)), "autotune_get")
+        names = {0: "default", 1: "1sm", 2: "2sm", 3: "mc2", 4: "mc4", 5: "n256"}
+        return {"variant": names.get(v[0].value, str(v[0].value)), "grid": v[1].value, "search_threads": v[2].value,
+                "search_bps": v[3].value, "ms": round(ms.value, 4)}
 
     def serve_start(self, max_inflight=8, max_batch=262144, path="fused_bf16"):
         c = ServeCfg(max_inflight=max_inflight, max_batch=max_batch,

@@ -157,7 +157,7 @@ struct TuneEntry {
     int search_threads = 0;  // threads per block of the search kernel (128 / 256 / 512)
     int search_bps = 0;      // resident blocks per SM the search grid is sized for
     int fused_grid = 0;      // persistent CTAs of the fused kernel (0 = one per SM)
-    int fused_variant = 0;   // 1 = 1-SM kernel, 2 = 2-SM pair kernel, 0 = library default
+    int fused_variant = 0;   // 0 = library default, 1 = N=128 1-SM, 2 = 2-SM pairs, 3 / 4 = clusters, 5 = N=256
     float ms = 0.f;          // best time measured by the tuner
 };
 

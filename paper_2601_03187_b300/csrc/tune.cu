@@ -1,7 +1,9 @@
 // Launch-shape autotuner: times the candidate launch shapes of a path on a caller-supplied
 // device batch and keeps the fastest per (ruleset, path). Candidates:
 //   search kernel (no-network, staged and plain paths): threads per block x blocks per SM;
-//   fused kernel: the number of persistent CTAs (one per SM, or a divisor-friendly subset so
+//   fused kernel: the tensor-core kernel variant (N=256; N=128 on one SM, on CTA pairs, or in
+//   clusters of 2 / 4 sharing weight tiles; the N=128 ones only for 6-block networks) and, for
+//   the N=256 kernel, the number of persistent CTAs (one per SM, or a divisor-friendly subset so
 //   that the tile count spreads evenly).
 #include <algorithm>
 
@@ -26,6 +28,7 @@ extern "C" int tang_autotune(tang_ctx *ctx, uint32_t rsh, const tang_header *d_h
     cudaSetDevice(ctx->device);
     std::vector<TuneEntry> cands;
     if (path == TANG_PATH_FUSED_BF16 || path == TANG_PATH_FUSED_FP8) {
+        if (!rs.model) return set_err(ctx, TANG_EINVAL, "ruleset %u has no model", rsh);
         const int sms = ctx->sm_count;
         const uint32_t tiles = (n + 127) / 128;
         std::vector<int> grids = {sms};
@@ -37,9 +40,16 @@ extern "C" int tang_autotune(tang_ctx *ctx, uint32_t rsh, const tang_header *d_h
             }
         for (int g : grids) {
             TuneEntry e;
+            e.fused_variant = 5;
             e.fused_grid = g;
             cands.push_back(e);
         }
+        if (rs.model->layers == 12)
+            for (int v : {1, 2, 3, 4}) {
+                TuneEntry e;
+                e.fused_variant = v;
+                cands.push_back(e);
+            }
     } else {
         for (int th : {128, 256, 512})
             for (int bps : {2, 4, 8, 16}) {
@@ -87,5 +97,20 @@ extern "C" int tang_autotune(tang_ctx *ctx, uint32_t rsh, const tang_header *d_h
     best.ms = best_ms;
     rs.tune[path] = best;
     drop_graphs_of(ctx);  // graphs captured the previous launch shape
+    return TANG_OK;
+}
+
+extern "C" int tang_autotune_get(tang_ctx *ctx, uint32_t rsh, uint32_t path, int *variant, int *grid, int *search_threads,
+                                 int *search_bps, float *ms) {
+    if (!ctx) return TANG_EINVAL;
+    auto it = ctx->rulesets.find(rsh);
+    if (it == ctx->rulesets.end()) return set_err(ctx, TANG_ENOTFOUND, "unknown ruleset %u", rsh);
+    auto t = it->second->tune.find(path & TANG_PATH_MASK);
+    const TuneEntry e = t == it->second->tune.end() ? TuneEntry{} : t->second;
+    if (variant) *variant = e.fused_variant;
+    if (grid) *grid = e.fused_grid;
+    if (search_threads) *search_threads = e.search_threads;
+    if (search_bps) *search_bps = e.search_bps;
+    if (ms) *ms = e.ms;
     return TANG_OK;
 }

@@ -94,6 +94,12 @@ def test_autotune_keeps_ids_exact():
         want = oc.classify(rules, h)
         for path in ("no_nn", "fused_bf16"):
             ctx.autotune(rs, d, path=path)
+            choice = ctx.autotune_get(rs, path)
+            assert choice["ms"] > 0
+            if path == "fused_bf16":
+                assert choice["variant"] in ("1sm", "2sm", "mc2", "mc4", "n256")
+            else:
+                assert choice["search_threads"] in (128, 256, 512) and choice["search_bps"] in (2, 4, 8, 16)
             ids = ids_dev(len(h))
             ctx.classify(rs, d, ids, path=path, graph=True)
             ctx.classify(rs, d, ids, path=path, graph=True)
