@@ -305,6 +305,14 @@ int tang_insert_rule(tang_ctx *ctx, uint32_t rs, const tang_rule *rule);
  * Errors: TANG_ENOTFOUND. */
 int tang_delete_rule(tang_ctx *ctx, uint32_t rs, uint32_t id);
 
+/* The live rules of ruleset rs (after any inserts and deletes), in ascending (priority, id), as
+ * host records: prefix values carry only their top `len` bits, the protocol of a wildcard rule is
+ * 0. With out == NULL only *n_out (the live count) is set; else cap must be >= that count.
+ * Together with a model blob this checkpoints a ruleset: tang_load_ruleset of the export builds
+ * the same classifier (restricted-insertion placements become exact ones, as in a rebuild).
+ * Errors: TANG_ENOTFOUND, TANG_EINVAL (cap too small). */
+int tang_export_rules(tang_ctx *ctx, uint32_t rs, tang_rule *out, uint32_t cap, uint32_t *n_out);
+
 /* Rules inserted since load whose lengths differ from their tuple's (the deferred-update
  * counter of §5.2.2). */
 int tang_suboptimal_count(tang_ctx *ctx, uint32_t rs, uint64_t *count);
@@ -419,6 +427,17 @@ int tang_rebuild_ruleset(tang_ctx *ctx, uint32_t rs, int *model_kept);
  * time. Synchronous. */
 int tang_du_apply(tang_ctx *ctx, uint32_t rs, int decision, const tang_header *samples, uint32_t n,
                   const tang_train_cfg *cfg, tang_train_report *report);
+
+/* Failure-path self-test of the bounded device waits (an addition of this library; the paper
+ * has none). Every persistent kernel here waits on barriers with a time limit; when one runs
+ * out, the kernel records it in the context's device error word, its other waits give up, and
+ * the next synchronising call returns TANG_ETIMEOUT. This launches a one-block kernel whose
+ * first warp waits on a barrier that nothing completes, with a limit of `limit_ms` (1-2000),
+ * while a second warp waits on another with a 10 s limit and leaves on the first warp's abort
+ * flag. Returns TANG_ETIMEOUT when the wait ran out as designed; the error word is then clear
+ * and the context usable. *elapsed_ms (may be NULL) receives the kernel's duration.
+ * Synchronous. Errors: TANG_EINVAL (limit out of range), TANG_EDEVICE. */
+int tang_selftest_wait_timeout(tang_ctx *ctx, uint32_t limit_ms, float *elapsed_ms);
 
 /* ---------------------------------------------------------------------------------------
  * Autotuning and serving

@@ -131,6 +131,8 @@ _SIGS = {
     "tang_du_apply": (_I, [_P, _U32, _I, _P, _U32, ctypes.POINTER(TrainCfg), ctypes.POINTER(TrainReport)]),
     "tang_classify_hybrid": (_I, [_P, _U32, _P, _U32, _P, ctypes.POINTER(HybridCfg), ctypes.POINTER(Stats)]),
     "tang_autotune_get": (_I, [_P, _U32, _U32] + [ctypes.POINTER(_I)] * 4 + [ctypes.POINTER(_F)]),
+    "tang_selftest_wait_timeout": (_I, [_P, _U32, ctypes.POINTER(_F)]),
+    "tang_export_rules": (_I, [_P, _U32, _P, _U32, ctypes.POINTER(_U32)]),
 }
 
 
@@ -380,6 +382,15 @@ class Context:
     def delete_rule(self, rs: int, rule_id: int):
         self._ck(lib.tang_delete_rule(self._h, rs, int(rule_id)), "delete_rule")
 
+    def export_rules(self, rs: int) -> np.ndarray:
+        """The live rules in ascending (priority, id) (tang_export_rules)."""
+        n = ctypes.c_uint32()
+        self._ck(lib.tang_export_rules(self._h, rs, None, 0, ctypes.byref(n)), "export_rules")
+        out = np.zeros(n.value, dtype=RULE_DTYPE)
+        if n.value:
+            self._ck(lib.tang_export_rules(self._h, rs, out.ctypes.data, n.value, ctypes.byref(n)), "export_rules")
+        return out
+
     def suboptimal_count(self, rs: int) -> int:
         c = ctypes.c_uint64()
         self._ck(lib.tang_suboptimal_count(self._h, rs, ctypes.byref(c)), "suboptimal_count")
@@ -481,6 +492,12 @@ class Context:
         names = {0: "default", 1: "1sm", 2: "2sm", 3: "mc2", 4: "mc4", 5: "n256"}
         return {"variant": names.get(v[0].value, str(v[0].value)), "grid": v[1].value, "search_threads": v[2].value,
                 "search_bps": v[3].value, "ms": round(ms.value, 4)}
+
+    def selftest_wait_timeout(self, limit_ms: int = 50):
+        """(return code, kernel ms) of tang_selftest_wait_timeout; TANG_ETIMEOUT is the designed outcome."""
+        ms = ctypes.c_float()
+        rc = lib.tang_selftest_wait_timeout(self._h, int(limit_ms), ctypes.byref(ms))
+        return rc, float(ms.value)
 
     def serve_start(self, max_inflight=8, max_batch=262144, path="fused_bf16"):
         c = ServeCfg(max_inflight=max_inflight, max_batch=max_batch,

@@ -88,7 +88,7 @@ using namespace tang;
     } while (0)
 
 // After a synchronisation point: report (and clear) error bits set by bounded device waits.
-static int check_device_error(tang_ctx *ctx) {
+int tang::check_device_error(tang_ctx *ctx) {
     int bits = 0;
     if (cudaMemcpy(&bits, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
         return set_err(ctx, TANG_EDEVICE, "reading the device error word failed");

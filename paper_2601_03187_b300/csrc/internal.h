@@ -222,6 +222,9 @@ struct tang_ctx {
 // ---------------------------------------------------------------------------------------
 namespace tang {
 int set_err(tang_ctx *ctx, int code, const char *fmt, ...);
+// After a synchronisation point: TANG_ETIMEOUT (and the error word cleared) if a bounded device
+// wait ran out since the last check, else TANG_OK.
+int check_device_error(tang_ctx *ctx);
 int ctx_alloc(tang_ctx *ctx, size_t bytes, void **p);
 void ctx_free(tang_ctx *ctx, void *p);
 int ensure_scratch(tang_ctx *ctx, size_t bytes);

@@ -2,6 +2,7 @@
 // incremental training and full retraining (theta, on the counter of rules that restricted
 // insertion placed in a tuple whose lengths differ from theirs), incremental training from the
 // deployed model, the full rebuild of the tuple space, and the hot swap of the new weights.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -126,6 +127,40 @@ int tang_du_apply(tang_ctx *ctx, uint32_t rsh, int decision, const tang_header *
     }
     if (rc) return rc;
     return tang_load_model(ctx, rsh, blob.data(), blob.size());
+}
+
+int tang_export_rules(tang_ctx *ctx, uint32_t rsh, tang_rule *out, uint32_t cap, uint32_t *n_out) {
+    if (!ctx || !n_out) return TANG_EINVAL;
+    Ruleset *rs = du_find(ctx, rsh);
+    if (!rs) return set_err(ctx, TANG_ENOTFOUND, "unknown ruleset %u", rsh);
+    const HostTSS &H = rs->host;
+    *n_out = uint32_t(H.pos_of_id.size());
+    if (!out) return TANG_OK;
+    if (cap < *n_out) return set_err(ctx, TANG_EINVAL, "export needs room for %u rules", *n_out);
+    std::vector<const DRule *> live;
+    live.reserve(H.pos_of_id.size());
+    for (const auto &kv : H.pos_of_id) live.push_back(&H.pool[kv.second]);
+    std::sort(live.begin(), live.end(), [](const DRule *a, const DRule *b) {
+        return a->prio < b->prio || (a->prio == b->prio && a->id < b->id);
+    });
+    for (size_t i = 0; i < live.size(); ++i) {
+        const DRule &d = *live[i];
+        tang_rule r{};
+        r.sip = d.sip;
+        r.dip = d.dip;
+        r.sp_lo = uint16_t(d.sp & 0xFFFFu);
+        r.sp_hi = uint16_t(d.sp >> 16);
+        r.dp_lo = uint16_t(d.dp & 0xFFFFu);
+        r.dp_hi = uint16_t(d.dp >> 16);
+        r.sip_len = uint8_t(meta_sip_len(d.meta));
+        r.dip_len = uint8_t(meta_dip_len(d.meta));
+        r.proto_wild = meta_proto_exact(d.meta) ? 0 : 1;
+        r.proto = uint8_t(meta_proto(d.meta));
+        r.priority = d.prio;
+        r.id = d.id;
+        out[i] = r;
+    }
+    return TANG_OK;
 }
 
 int tang_graph_count(tang_ctx *ctx, uint32_t *count) {
