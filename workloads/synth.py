@@ -95,11 +95,12 @@ def gen_clustered_rules(
     p_block_len: float = 0.97,
     first_id: int = 0,
     priority_range: int | None = None,
+    lengths=(8, 16, 24, 32),
 ) -> np.ndarray:
     """Rules clustered in address blocks, each block with its own typical prefix lengths.
 
     n_blocks distinct (SIP /8, DIP /8) pairs are drawn; every block gets a (SIP length, DIP
-    length) pair uniform over {8,16,24,32}^2. A rule picks a block uniformly, takes the block's
+    length) pair uniform over lengths^2 (default {8,16,24,32}^2; all lengths must be >= 8). A rule picks a block uniformly, takes the block's
     lengths with probability p_block_len (else uniform lengths from the same set), and random
     address bits below the block's /8. Ports and protocol as gen_rules' defaults. Priorities are
     uniform draws from [0, priority_range) (default: a permutation of 0..n-1); ids are
@@ -111,7 +112,8 @@ def gen_clustered_rules(
     pairs = rng.choice(1 << 16, n_blocks, replace=False)
     b_sip = (pairs >> 8).astype(np.uint32) << np.uint32(24)
     b_dip = (pairs & 0xFF).astype(np.uint32) << np.uint32(24)
-    lens = np.array([8, 16, 24, 32], dtype=np.int64)
+    lens = np.array(lengths, dtype=np.int64)
+    assert lens.min() >= 8 and lens.max() <= 32
     b_ls = rng.choice(lens, n_blocks)
     b_ld = rng.choice(lens, n_blocks)
     blk = rng.integers(0, n_blocks, n)
