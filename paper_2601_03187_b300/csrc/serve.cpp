@@ -54,6 +54,7 @@ struct ServeEngine {
     std::condition_variable cv_work, cv_done;
     std::thread worker;
     bool stop = false;
+    bool slot_finished = false;  // set by a stream callback: some slot's work completed
     uint64_t next_id = 1;
 };
 
@@ -62,37 +63,39 @@ double now_s() { return std::chrono::duration<double>(std::chrono::steady_clock:
 int enqueue_classify_path(tang_ctx *ctx, uint32_t rs, const tang_header *h, uint32_t n, uint32_t *ids, uint32_t path,
                           cudaStream_t st);
 
+// Runs on a CUDA driver thread after a slot's D2H copy: wakes the worker (no CUDA calls here).
+static void CUDART_CB slot_done(void *arg) {
+    ServeEngine *E = static_cast<ServeEngine *>(arg);
+    {
+        std::lock_guard<std::mutex> g(E->mu);
+        E->slot_finished = true;
+    }
+    E->cv_work.notify_one();
+}
+
+// The worker. The engine lock guards the queue and the requests' bookkeeping only; host copies
+// (staging headers, delivering ids) and CUDA calls run outside it, so submitters and pollers
+// are not held up by the copies.
 static void serve_loop(ServeEngine *E) {
     tang_ctx *ctx = E->ctx;
     cudaSetDevice(ctx->device);
+    std::vector<ServeSlot *> finished, launched;
+    std::vector<uint32_t> launched_rs;
     std::unique_lock<std::mutex> lk(E->mu);
     while (true) {
-        // 1. retire finished slots
-        bool progressed = false;
-        for (auto &s : E->slots) {
-            if (!s.busy) continue;
-            if (cudaEventQuery(s.ev) != cudaSuccess) continue;
-            const double t = now_s();
-            for (const Piece &p : s.pieces) {
-                std::memcpy(p.req->ids + p.off, s.p_ids + p.slot_off, sizeof(uint32_t) * p.n);
-                if (--p.req->outstanding == 0 && p.req->next == p.req->n) {
-                    p.req->done = true;
-                    p.req->done_s = t;
-                }
-            }
-            s.pieces.clear();
-            s.busy = false;
-            progressed = true;
-        }
-        if (progressed) E->cv_done.notify_all();
-        // 2. admit queued work into free slots
+        // 1. slots whose work completed (their pieces are read below without the lock)
+        finished.clear();
+        for (auto &s : E->slots)
+            if (s.busy && cudaEventQuery(s.ev) == cudaSuccess) finished.push_back(&s);
+        E->slot_finished = false;
+        // 2. pack queued requests of one ruleset (FIFO, up to max_batch) into each free slot
+        launched.clear();
+        launched_rs.clear();
+        const double t_pack = now_s();
         for (auto &s : E->slots) {
             if (s.busy || E->queue.empty()) continue;
-            Request *head = E->queue.front();
-            const uint32_t rs = head->rs;
+            const uint32_t rs = E->queue.front()->rs;
             uint32_t used = 0;
-            const double t = now_s();
-            // pack requests of the head's ruleset in arrival order
             for (auto it = E->queue.begin(); it != E->queue.end() && used < E->cfg.max_batch;) {
                 Request *r = *it;
                 if (r->rs != rs) {
@@ -100,8 +103,7 @@ static void serve_loop(ServeEngine *E) {
                     continue;
                 }
                 const uint32_t take = std::min(E->cfg.max_batch - used, r->n - r->next);
-                if (r->next == 0) r->start_s = t;
-                std::memcpy(s.p_h + used, r->h + r->next, sizeof(tang_header) * take);
+                if (r->next == 0) r->start_s = t_pack;
                 s.pieces.push_back(Piece{r, r->next, take, used});
                 r->next += take;
                 r->outstanding++;
@@ -112,26 +114,61 @@ static void serve_loop(ServeEngine *E) {
                     break;  // the slot is full
             }
             if (used == 0) continue;
+            s.busy = true;
+            launched.push_back(&s);
+            launched_rs.push_back(rs);
+        }
+        lk.unlock();
+        // 3. deliver the finished slots' ids to their requests
+        for (ServeSlot *s : finished)
+            for (const Piece &p : s->pieces)
+                std::memcpy(p.req->ids + p.off, s->p_ids + p.slot_off, sizeof(uint32_t) * p.n);
+        // 4. stage and launch the packed slots: H2D, classify, D2H, then a completion callback
+        for (size_t k = 0; k < launched.size(); ++k) {
+            ServeSlot &s = *launched[k];
+            uint32_t used = 0;
+            for (const Piece &p : s.pieces) {
+                std::memcpy(s.p_h + p.slot_off, p.req->h + p.off, sizeof(tang_header) * p.n);
+                used = std::max(used, p.slot_off + p.n);
+            }
             cudaMemcpyAsync(s.d_h, s.p_h, sizeof(tang_header) * used, cudaMemcpyHostToDevice, s.st);
-            int rc = enqueue_classify_path(ctx, rs, static_cast<tang_header *>(s.d_h), used,
-                                           static_cast<uint32_t *>(s.d_ids), E->cfg.path, s.st);
+            const int rc = enqueue_classify_path(ctx, launched_rs[k], static_cast<tang_header *>(s.d_h), used,
+                                                 static_cast<uint32_t *>(s.d_ids), E->cfg.path, s.st);
             if (rc)
                 for (const Piece &p : s.pieces) p.req->rc = rc;
             cudaMemcpyAsync(s.p_ids, s.d_ids, sizeof(uint32_t) * used, cudaMemcpyDeviceToHost, s.st);
             cudaEventRecord(s.ev, s.st);
-            s.busy = true;
+            cudaLaunchHostFunc(s.st, slot_done, E);
+        }
+        lk.lock();
+        // 5. bookkeeping of the delivered pieces; free their slots
+        if (!finished.empty()) {
+            const double t = now_s();
+            for (ServeSlot *s : finished) {
+                for (const Piece &p : s->pieces)
+                    if (--p.req->outstanding == 0 && p.req->next == p.req->n) {
+                        p.req->done = true;
+                        p.req->done_s = t;
+                    }
+                s->pieces.clear();
+                s->busy = false;
+            }
+            E->cv_done.notify_all();
+            continue;  // a slot is free: look at the queue again at once
         }
         bool any_busy = false;
         for (auto &s : E->slots) any_busy |= s.busy;
         if (E->stop && E->queue.empty() && !any_busy) break;
-        if (any_busy) {
-            // poll completions at a short interval while work is in flight
-            lk.unlock();
-            std::this_thread::sleep_for(std::chrono::microseconds(20));
-            lk.lock();
-        } else {
-            E->cv_work.wait_for(lk, std::chrono::milliseconds(5));
-        }
+        if (!launched.empty()) continue;
+        // 6. sleep until a slot completes or the engine stops. An idle GPU takes new work at once;
+        // while launches are in flight, requests arriving within a short window are batched into
+        // one launch instead of one small launch each (many small concurrent kernels contend for
+        // the SMs and lengthen every request's latency)
+        if (any_busy)
+            E->cv_work.wait_for(lk, std::chrono::microseconds(100), [&] { return E->slot_finished || E->stop; });
+        else
+            E->cv_work.wait_for(lk, std::chrono::milliseconds(5),
+                                [&] { return E->slot_finished || E->stop || !E->queue.empty(); });
     }
 }
 
