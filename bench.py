@@ -149,13 +149,21 @@ def barrier(world):
 
 
 def max_over_ranks(x, world):
+    """The largest of the ranks' values of x (the slowest rank's time defines the job's)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_mpkts(packets_per_rank, steps, dt_max, world):
+    """Whole-job throughput in Mpkt/s: every rank classified `steps` batches of
+    `packets_per_rank` packets, and the slowest rank took `dt_max` seconds."""
+    return world * packets_per_rank * steps / dt_max / 1e6
 
 
 def workload():
@@ -632,7 +640,7 @@ def main():
     with ClockSampler(local) as clk:
         dt = time_path("fused_bf16", args.steps, args.warmup)
     dt = max_over_ranks(dt, world)
-    value = world * n * args.steps / dt / 1e6
+    value = job_mpkts(n, args.steps, dt, world)
     ids_fused = ids.cpu().numpy().view(np.uint32)
     st_bf16 = ctx.classify(rs, d_h, ids, path="fused_bf16", stats=True, variant=args.variant)
 
@@ -752,7 +760,7 @@ def main():
     for _ in range(e2e_steps):
         ctx.classify(rs, hh, pout, path="fused_bf16")
     e2e_dt = max_over_ranks(time.perf_counter() - t0, world)
-    e2e = world * n * e2e_steps / e2e_dt / 1e6
+    e2e = job_mpkts(n, e2e_steps, e2e_dt, world)
     e2e_equal = bool((pout == ids_fused).all())
 
     # ---- CPU baseline: the oracle on a bounded sample, all host cores (rank 0 only)
