@@ -602,12 +602,14 @@ int tc_prepare_model(tang_ctx *ctx, DeviceModel &m) {
     // the tensor-core kernels are built for N = 512; the N=256 kernel takes any block count up to
     // 31 (the N=128 variants only the paper's 6)
     if (N != 512 || m.blocks < 1 || m.blocks > 31) return TANG_OK;
-    if (C > 128) return TANG_OK;
+    // the N=128 variants take up to 128 classes; the N=256 kernel any count, in 256-row output
+    // tiles (padded with zero rows past Cpad)
+    const bool narrow = C <= 128;
     const int nl = int(2 * m.blocks);  // N x N layers
     m.layers = uint32_t(nl);
-    const uint32_t Cpad = m.Cpad;  // multiple of 16
+    const uint32_t Cpad = m.Cpad;  // multiple of 32
     const size_t hid = size_t(nl) * N * N;
-    const size_t rows_out = Cpad;
+    const size_t rows_out = Cpad <= 256 ? Cpad : (Cpad + 255) / 256 * 256;
     const float *hp = m.host_params.data();
     // host views of the FP32 parameters
     const float *W0 = hp;
@@ -633,7 +635,7 @@ int tc_prepare_model(tang_ctx *ctx, DeviceModel &m) {
             for (uint32_t k = 0; k < N; ++k) wb[size_t(l) * N * N + size_t(n) * N + k] = __float2bfloat16_rn(W[l][size_t(k) * N + n]);
         for (uint32_t n = 0; n < N; ++n) bias[size_t(l) * N + n] = B[l][n];
     }
-    for (uint32_t c = 0; c < Cpad; ++c)
+    for (uint32_t c = 0; c < rows_out; ++c)
         for (uint32_t k = 0; k < N; ++k)
             wb[hid + size_t(c) * N + k] = __float2bfloat16_rn(c < C ? Wc[size_t(k) * C + c] : 0.f);
     for (uint32_t c = 0; c < C; ++c) bias[size_t(nl) * N + c] = bc[c];
@@ -644,13 +646,15 @@ int tc_prepare_model(tang_ctx *ctx, DeviceModel &m) {
     cudaMemcpy(m.d_bias_tc, bias.data(), bias.size() * 4, cudaMemcpyHostToDevice);
     // one map pair per cluster size 1, 2, 4: a CTA loads 128/CS rows of each hidden tile and
     // Cpad/CS rows of each output tile
-    TcMaps *maps = static_cast<TcMaps *>(aligned_alloc(64, 3 * sizeof(TcMaps)));
-    m.tmap_bf16 = maps;
-    for (int ci = 0; ci < 3; ++ci) {
-        const uint32_t cs = 1u << ci;
-        if ((rc = make_tmap(ctx, &maps[ci].hid, m.d_wbf16, nl * N, false, 128 / cs))) return rc;
-        if ((rc = make_tmap(ctx, &maps[ci].out, static_cast<__nv_bfloat16 *>(m.d_wbf16) + hid, Cpad, false, Cpad / cs)))
-            return rc;
+    if (narrow) {
+        TcMaps *maps = static_cast<TcMaps *>(aligned_alloc(64, 3 * sizeof(TcMaps)));
+        m.tmap_bf16 = maps;
+        for (int ci = 0; ci < 3; ++ci) {
+            const uint32_t cs = 1u << ci;
+            if ((rc = make_tmap(ctx, &maps[ci].hid, m.d_wbf16, nl * N, false, 128 / cs))) return rc;
+            if ((rc = make_tmap(ctx, &maps[ci].out, static_cast<__nv_bfloat16 *>(m.d_wbf16) + hid, Cpad, false, Cpad / cs)))
+                return rc;
+        }
     }
 
     if (m.has_fp8) {
@@ -691,16 +695,18 @@ int tc_prepare_model(tang_ctx *ctx, DeviceModel &m) {
             }
         if ((rc = ctx_alloc(ctx, fold.size() * 4, (void **)&m.d_fold8))) return rc;
         cudaMemcpy(m.d_fold8, fold.data(), fold.size() * 4, cudaMemcpyHostToDevice);
-        TcMaps *m8 = static_cast<TcMaps *>(aligned_alloc(64, 3 * sizeof(TcMaps)));
-        m.tmap_fp8 = m8;
-        for (int ci = 0; ci < 3; ++ci) {
-            const uint32_t cs = 1u << ci;
-            if ((rc = make_tmap(ctx, &m8[ci].hid, m.d_wfp8, nl * N, true, 128 / cs))) return rc;
-            if ((rc = make_tmap(ctx, &m8[ci].out, static_cast<uint8_t *>(m.d_wfp8) + hid, Cpad, true, Cpad / cs)))
-                return rc;
+        if (narrow) {
+            TcMaps *m8 = static_cast<TcMaps *>(aligned_alloc(64, 3 * sizeof(TcMaps)));
+            m.tmap_fp8 = m8;
+            for (int ci = 0; ci < 3; ++ci) {
+                const uint32_t cs = 1u << ci;
+                if ((rc = make_tmap(ctx, &m8[ci].hid, m.d_wfp8, nl * N, true, 128 / cs))) return rc;
+                if ((rc = make_tmap(ctx, &m8[ci].out, static_cast<uint8_t *>(m.d_wfp8) + hid, Cpad, true, Cpad / cs)))
+                    return rc;
+            }
         }
     }
-    if (nl == tc::kLayers && (rc = tc2_prepare_model(ctx, m))) return rc;
+    if (narrow && nl == tc::kLayers && (rc = tc2_prepare_model(ctx, m))) return rc;
     if ((rc = tc256_prepare_model(ctx, m))) return rc;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return set_err(ctx, TANG_EDEVICE, "tc_prepare_model: %s", cudaGetErrorString(e));
@@ -769,8 +775,7 @@ int tc_launch(tang_ctx *ctx, Ruleset &rs, const tang_header *h, uint32_t n, uint
     if (n == 0) return TANG_OK;
     DeviceModel &m = *rs.model;
     const bool f8 = precision == TANG_FP8;
-    const TcMaps *maps = static_cast<const TcMaps *>(f8 ? m.tmap_fp8 : m.tmap_bf16);
-    if (!maps) return set_err(ctx, TANG_EUNSUPPORTED, "no tensor-core copy of this model");
+    if (!m.d_wbf16 || (f8 && !m.d_wfp8)) return set_err(ctx, TANG_EUNSUPPORTED, "no tensor-core copy of this model");
     TcParams prm{};
     prm.headers = h;
     prm.n = n;
@@ -799,14 +804,17 @@ int tc_launch(tang_ctx *ctx, Ruleset &rs, const tang_header *h, uint32_t n, uint
     prm.trace = d_trace;
 #endif
     int v = variant ? variant : (tune && tune->fused_variant ? tune->fused_variant : kDefaultVariant);
-    if (m.layers != uint32_t(tc::kLayers)) v = 5;  // the N=128 variants are built for 6 blocks
+    // the N=128 variants are built for 6 blocks and at most 128 classes
+    const bool narrow6 = m.layers == uint32_t(tc::kLayers) && m.C <= 128;
+    if (!narrow6) v = 5;
     if (v == 2 || v == 5) {
         const int rc = v == 2 ? tc2_launch(ctx, m, prm, f8, st, tune ? tune->fused_grid : 0)
                               : tc256_launch(ctx, m, prm, f8, st, tune ? tune->fused_grid : 0);
         if (rc != TANG_EUNSUPPORTED) return rc;  // models without those maps run the 1-SM N=128 kernel
     }
-    if (m.layers != uint32_t(tc::kLayers))
-        return set_err(ctx, TANG_EUNSUPPORTED, "no tensor-core kernel for a %u-block model", m.blocks);
+    const TcMaps *maps = static_cast<const TcMaps *>(f8 ? m.tmap_fp8 : m.tmap_bf16);
+    if (!narrow6 || !maps)
+        return set_err(ctx, TANG_EUNSUPPORTED, "no tensor-core kernel for a %u-block, %u-class model", m.blocks, m.C);
     // variants 1, 3, 4: the 1-SM kernel with weight tiles shared by clusters of 1, 2, 4 CTAs
     const int ci = v == 3 ? 1 : v == 4 ? 2 : 0;
     int rc = ci == 0 ? (f8 ? launch_1sm<true, 1>(ctx, maps[0], prm, st, tune) : launch_1sm<false, 1>(ctx, maps[0], prm, st, tune))

@@ -111,6 +111,10 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nl = int(p.layers);  // N x N layers: 2 per residual block
+    // the output layer in 256-column chunks (Cpad is a multiple of 32; the weight rows are padded
+    // to whole 256-row tiles when Cpad > 256, so every tile load is in bounds)
+    const int n_oc = int((p.Cpad + 255) >> 8);
+    const uint32_t out_box = p.Cpad < 256 ? p.Cpad : 256u;
     constexpr int KB = F8 ? 4 : 8;
     constexpr int KBW = F8 ? 128 : 64;
     constexpr uint32_t kActArrivals = F8 ? 8 : 4;  // 64-column units per K-block x 4 lane quadrants
@@ -185,7 +189,7 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
                     advance();
                 }
                 for (int L = 0; L <= nl && ok; ++L) {
-                    const int nch = L == nl ? 1 : 2;
+                    const int nch = L == nl ? n_oc : 2;
                     for (int c = 0; c < nch && ok; ++c)
                         for (int kb = 0; kb < KB; ++kb) {
                             uint8_t *dst = next_stage();
@@ -194,8 +198,8 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
                                 ptx::mbar_arrive_expect_tx(&full[stage], kStageBytes);
                                 ptx::tma_load_2d(dst, &tm_hid, &full[stage], kb * KBW, L * kHid + c * 256);
                             } else {
-                                ptx::mbar_arrive_expect_tx(&full[stage], p.Cpad * 128);
-                                ptx::tma_load_2d(dst, &tm_out, &full[stage], kb * KBW, 0);
+                                ptx::mbar_arrive_expect_tx(&full[stage], out_box * 128);
+                                ptx::tma_load_2d(dst, &tm_out, &full[stage], kb * KBW, c * 256);
                             }
                             advance();
                         }
@@ -213,7 +217,6 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
         // bounds the tensor pipe's, so it keeps no state in captured lambdas or local memory.
         if (lane == 0) {
             const uint32_t idesc_h = ptx::idesc_make(128, 256, F8);
-            const uint32_t idesc_o = ptx::idesc_make(128, p.Cpad, F8);
             const uint32_t idesc_0 = ptx::idesc_make(128, 256, false);  // layer 0: BF16 on both paths
             const uint32_t y_addr = ptx::smem_u32(sY), st_addr = ptx::smem_u32(sStage);
             const uint64_t a0_desc = ptx::sdesc_sw128(y_addr);
@@ -251,9 +254,10 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
                 }
                 for (int L = 0; L <= nl && !err; ++L, ++lay) {
                     const bool a_tmem = (L & 1) == 0;  // FC1 and the output layer read x from TMEM
-                    const int nch = L == nl ? 1 : 2;
-                    const uint32_t idesc = L == nl ? idesc_o : idesc_h;
+                    const int nch = L == nl ? n_oc : 2;
                     for (int c = 0; c < nch && !err; ++c, ++uses) {
+                        const uint32_t idesc =
+                            L == nl ? ptx::idesc_make(128, p.Cpad - 256u * c < 256u ? p.Cpad - 256u * c : 256u, F8) : idesc_h;
                         TC_TRACE(trace::kMma + uses * 12 + 0, uses < uint32_t(trace::kChunks));
                         if (!ptx::mbar_wait(acc_empty, (uses - 1) & 1, sAbort, kTimeoutNs)) {
                             err = 2;
@@ -520,43 +524,46 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
                 }
             }
             if (!ok) break;
-            // ---- output layer: each column group takes a quarter of the logits; the kArgG
-            // warps combine the four partial maxima per row and hand the prediction on
+            // ---- output layer, in 256-column chunks: each column group takes a quarter of every
+            // chunk; the kArgG warps combine the four partial maxima per row and hand the
+            // prediction on
             {
-                if (!ptx::mbar_wait(acc_full, uses & 1, sAbort, kTimeoutNs)) {
-                    fail(32);
-                    ok = false;
-                    break;
-                }
-                ++uses;
-                ptx::tc_fence_after();
                 float best = -INFINITY;
                 int arg = 0;
-                {
-                    const uint32_t cq = p.Cpad / 4;  // a multiple of 8
-                    const float *bias = p.bias + nl * kHid;
-                    const float *dq = F8 ? p.dq + nl * kHid : nullptr;
+                const float *bias = p.bias + nl * kHid;
+                const float *dq = F8 ? p.dq + nl * kHid : nullptr;
+                for (int oc = 0; oc < n_oc; ++oc) {
+                    if (!ptx::mbar_wait(acc_full, uses & 1, sAbort, kTimeoutNs)) {
+                        fail(32);
+                        ok = false;
+                        break;
+                    }
+                    ++uses;
+                    ptx::tc_fence_after();
+                    const uint32_t c_base = 256u * uint32_t(oc);
+                    const uint32_t cq = (p.Cpad - c_base < 256u ? p.Cpad - c_base : 256u) / 4;  // a multiple of 8
                     for (uint32_t c0 = uint32_t(g) * cq; c0 < uint32_t(g + 1) * cq; c0 += 8) {
                         uint32_t a[8];
                         ptx::tmem_ld8(tmem + lane_base + c0, a);
                         ptx::tmem_wait_ld();
 #pragma unroll
                         for (int j = 0; j < 8; ++j) {
-                            const uint32_t cc = c0 + j;
+                            const uint32_t cc = c_base + c0 + j;
                             if (cc >= p.C) break;
                             float z = __uint_as_float(a[j]);
                             z = F8 ? fmaf(z, __ldg(dq + cc), __ldg(bias + cc)) : z + __ldg(bias + cc);
                             if (p.logits && i < p.n) p.logits[size_t(i) * p.C + cc] = z;
-                            if (z > best) {  // first index of the maximum, as a serial scan
+                            if (z > best) {  // this group's columns in increasing order: the first maximum
                                 best = z;
                                 arg = int(cc);
                             }
                         }
                     }
+                    ptx::tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) ptx::mbar_arrive(acc_empty);
                 }
-                ptx::tc_fence_before();
-                __syncwarp();
-                if (lane == 0) ptx::mbar_arrive(acc_empty);
+                if (!ok) break;
                 const uint32_t t = tcnt & 1, tu = tcnt >> 1;  // this CTA's tile count: barrier parities
                 ++tcnt;
                 if (g != kArgG) {
@@ -570,14 +577,15 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
                         ok = false;
                         break;
                     }
-                    // groups in column order, strict > keeps the lowest column among equal maxima
+                    // the lowest column among equal maxima, as a serial scan (with several chunks
+                    // a group's columns interleave with the others', so ties compare indices)
                     float b = sPartBest[r];
                     int am = sPartArg[r];
 #pragma unroll
                     for (int gg = 1; gg < 4; ++gg) {
                         const float bg = gg == kArgG ? best : sPartBest[gg * kM + r];
                         const int ag = gg == kArgG ? arg : sPartArg[gg * kM + r];
-                        if (bg > b) {
+                        if (bg > b || (bg == b && ag < am)) {
                             b = bg;
                             am = ag;
                         }
@@ -695,8 +703,8 @@ void layer0_operand(const float *W0, const float *b0, float s, __nv_bfloat16 *B)
 }
 }  // namespace
 
-// 256-row hidden-layer maps (the output-layer map of the 1-SM kernel is reused) and the layer-0
-// operands with their maps.
+// 256-row hidden-layer maps, output-layer maps of up to 256-row tiles, and the layer-0 operands
+// with their maps.
 int tc256_prepare_model(tang_ctx *ctx, DeviceModel &m) {
     if (!m.d_wbf16) return TANG_OK;
     Tc256Maps *maps = static_cast<Tc256Maps *>(aligned_alloc(64, 2 * sizeof(Tc256Maps)));
@@ -708,13 +716,14 @@ int tc256_prepare_model(tang_ctx *ctx, DeviceModel &m) {
     int rc = ctx_alloc(ctx, l0.size() * 2, &m.d_l0);
     if (rc) return rc;
     cudaMemcpy(m.d_l0, l0.data(), l0.size() * 2, cudaMemcpyHostToDevice);
-    const TcMaps *one = static_cast<const TcMaps *>(m.tmap_bf16);
-    maps[0].out = one[0].out;
+    // output tiles of min(Cpad, 256) rows; past 256 the copies hold whole 256-row tiles
+    const size_t hid = size_t(m.layers) * m.N * m.N;
+    const uint32_t out_rows = m.Cpad <= 256 ? m.Cpad : (m.Cpad + 255) / 256 * 256, out_box = std::min<uint32_t>(m.Cpad, 256);
+    if ((rc = make_tmap(ctx, &maps[0].out, static_cast<__nv_bfloat16 *>(m.d_wbf16) + hid, out_rows, false, out_box))) return rc;
     if ((rc = make_tmap(ctx, &maps[0].hid, m.d_wbf16, m.layers * m.N, false, 256))) return rc;
     if ((rc = make_tmap(ctx, &maps[0].l0, m.d_l0, 512, false, 256, tc256::kL0K))) return rc;
     if (m.d_wfp8) {
-        const TcMaps *one8 = static_cast<const TcMaps *>(m.tmap_fp8);
-        maps[1].out = one8[0].out;
+        if ((rc = make_tmap(ctx, &maps[1].out, static_cast<uint8_t *>(m.d_wfp8) + hid, out_rows, true, out_box))) return rc;
         if ((rc = make_tmap(ctx, &maps[1].hid, m.d_wfp8, m.layers * m.N, true, 256))) return rc;
         rc = make_tmap(ctx, &maps[1].l0, static_cast<__nv_bfloat16 *>(m.d_l0) + size_t(512) * tc256::kL0K, 512, false,
                        256, tc256::kL0K);

@@ -8,7 +8,7 @@ import paper_2601_03187_b300 as tg
 import workloads as wl
 from gpu_util import ids_dev, ids_host, logit_tolerance, random_params, to_dev
 from oracle import classify as oc
-from oracle import mlp, quant
+from oracle import mlp, quant, tss
 
 pytestmark = pytest.mark.gpu
 
@@ -164,6 +164,57 @@ def test_other_depths_on_the_n256_kernel(blocks):
         q = bf16_weights(p64) if prec == "bf16" else e4m3_weights(p64)
         z64 = mlp.forward(q, X)
         for variant in (None, "1sm"):  # "1sm" falls back to the N=256 kernel for these depths
+            z, tup = infer(ctx, rs, h[:4096], T, tg.BF16 if prec == "bf16" else tg.FP8, variant)
+            tol = logit_tolerance(q, X, U32, U_BF16 if prec == "bf16" else U_E4M3)
+            assert np.isfinite(z).all()
+            assert (np.abs(z - z64) <= tol).all(), (prec, float((np.abs(z - z64) / tol).max()))
+            assert (tup == np.argmax(z, axis=1)).all()
+    want = oc.classify(rules, h)
+    d = to_dev(h)
+    for path in ("fused_bf16", "fused_fp8", "staged_bf16", "plain_fp32"):
+        ids = ids_dev(len(h))
+        ctx.classify(rs, d, ids, path=path)
+        torch.cuda.synchronize()
+        assert (ids_host(ids) == want).all(), path
+    ctx.close()
+
+
+def _spread_rules(n, seed):
+    """n rules with SIP / DIP prefix lengths uniform in 0..32: hundreds of tuples."""
+    rng = np.random.default_rng(seed)
+    rules = wl.gen_rules(n, seed)
+    for f in ("sip", "dip"):
+        rules[f + "_len"] = rng.integers(0, 33, n)
+        m = np.array([tss.prefix_mask(int(l)) for l in rules[f + "_len"]], dtype=np.uint64)
+        rules[f] = (rules[f].astype(np.uint64) & m).astype(np.uint32)
+    return rules
+
+
+@pytest.mark.parametrize("n_rules", [200, 350, 1500])
+def test_many_tuples_on_the_n256_kernel(n_rules):
+    """Rulesets with 187, 308 and 824 tuples on the N=256 kernel, whose output layer then runs
+    as one chunk of 192 columns, as 256 + 64, and as three of 256 + 64: logits within the bound
+    of the float64 forward of the quantised weights, argmax = the first maximum, ids exact."""
+    ctx = tg.Context(0)
+    rules = _spread_rules(n_rules, 300 + n_rules)
+    rs = ctx.load_ruleset(rules)
+    T = ctx.ruleset_info(rs)["n_tuples"]
+    assert T == {200: 187, 350: 308, 1500: 824}[n_rules], T
+    blocks = 2
+    p = random_params(np.random.default_rng(n_rules), N=512, blocks=blocks, C=T)
+    h = wl.gen_trace(rules, [("inside", 9000), ("random", 1000)], 31)
+    X = mlp.features(h[:4096])
+    p64 = {k: ([a.astype(np.float64) for a in v] if isinstance(v, list) else v.astype(np.float64)) for k, v in p.items()}
+    _, cache = mlp.forward(p64, X, keep=True)
+    amax = []
+    for k in range(blocks):
+        amax += [np.abs(cache["h_in"][k]).max(), np.abs(cache["u"][k]).max()]
+    amax.append(np.abs(cache["h_out"]).max())
+    ctx.load_model(rs, tg.pack_model(p, np.array(amax, dtype=np.float32)))
+    for prec in ("bf16", "fp8"):
+        q = bf16_weights(p64) if prec == "bf16" else e4m3_weights(p64)
+        z64 = mlp.forward(q, X)
+        for variant in (None, "1sm"):  # "1sm" falls back to the N=256 kernel past 128 classes
             z, tup = infer(ctx, rs, h[:4096], T, tg.BF16 if prec == "bf16" else tg.FP8, variant)
             tol = logit_tolerance(q, X, U32, U_BF16 if prec == "bf16" else U_E4M3)
             assert np.isfinite(z).all()
