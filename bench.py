@@ -409,7 +409,15 @@ def measure_deferred_update(tg, ctx, n_rules=65536, windows=10, per_window=2000,
             "runs": runs}
 
 
-def measure_model_sizes(tg, ctx, n_rules=65536, train_s=6.0, n_eval=1 << 22):
+MODEL_SHAPES = {
+    # (width, blocks): the paper's width at four depths, and two narrower networks
+    "default": ((512, 1), (512, 2), (512, 3), (512, 6), (256, 2), (128, 2)),
+    # widths 64-512 x 1, 2, 3, 6 residual blocks
+    "full": tuple((w, b) for w in (512, 256, 128, 64) for b in (1, 2, 3, 6)),
+}
+
+
+def measure_model_sizes(tg, ctx, n_rules=65536, train_s=6.0, n_eval=1 << 22, shapes=MODEL_SHAPES["default"]):
     """Model size against accuracy and speed (§6.1 weighs the network's capacity against its
     inference cost). One clustered ruleset (as in the dynamic experiment: a learnable mapping),
     the same training time for every shape, then per shape: held-out accuracy, the network's
@@ -427,7 +435,7 @@ def measure_model_sizes(tg, ctx, n_rules=65536, train_s=6.0, n_eval=1 << 22):
     exact = torch.empty(len(ev), dtype=torch.int32, device="cuda")
     ctx.classify(rs, d, exact, path="no_nn")
     rows = []
-    for width, blocks in ((512, 1), (512, 2), (512, 3), (512, 6), (256, 2), (128, 2)):
+    for width, blocks in shapes:
         blob, rep = ctx.train(rs, train_h, N=width, blocks=blocks, batch=8192, epochs=1000, max_rounds=1, alpha=100,
                               holdout=0.05, time_budget_s=train_s, seed=73)
         ctx.load_model(rs, blob)
@@ -579,6 +587,8 @@ def main():
     ap.add_argument("--train-seconds", type=float, default=float(os.environ.get("TANG_TRAIN_SECONDS", "20")))
     ap.add_argument("--quick", action="store_true", help="skip the secondary measurements")
     ap.add_argument("--no-du", action="store_true", help="skip the deferred-update experiment")
+    ap.add_argument("--sizes", default="default", choices=sorted(MODEL_SHAPES),
+                    help="network shapes of the model-size sweep (full: widths 64-512 x 1, 2, 3, 6 blocks)")
     ap.add_argument("--packets", type=int, default=N_PACKETS, help="use the first P packets of the trace")
     ap.add_argument("--variant", default=None, choices=[None, "1sm", "2sm"],
                     help="tensor-core kernel variant (default: the library's choice)")
@@ -746,7 +756,7 @@ def main():
         extra["updates"] = measure_updates(tg, ctx)
         if not args.no_du:
             extra["deferred_update"] = measure_deferred_update(tg, ctx)
-            extra["model_sizes"] = measure_model_sizes(tg, ctx)
+        extra["model_sizes"] = measure_model_sizes(tg, ctx, shapes=MODEL_SHAPES[args.sizes])
 
     # ---- e2e: host (pinned) buffers through the C ABI, copies inside the timed region
     ph = torch.empty(n * 16, dtype=torch.uint8, pin_memory=True).numpy()
