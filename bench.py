@@ -423,8 +423,8 @@ def measure_model_sizes(tg, ctx, n_rules=65536, train_s=6.0, n_eval=1 << 22, sha
     the same training time for every shape, then per shape: held-out accuracy, the network's
     tuple accuracy and the paper-mode classification accuracy (the "Classi. Accu." of Tables 2-3)
     on a separate trace, the exact search's probes per packet, and the exact classification
-    throughput on the tensor-core kernel (width 512; depth from 1 to 6 residual blocks) or, for
-    narrower networks, which only the FP32 path serves, on that path."""
+    throughput on the tensor-core kernel (widths 256 and 512, any depth) or, for narrower networks,
+    which only the FP32 path serves, on that path."""
     import torch
     rules = wl.gen_clustered_rules(n_rules, 70)
     rs = ctx.load_ruleset(rules)
@@ -439,11 +439,11 @@ def measure_model_sizes(tg, ctx, n_rules=65536, train_s=6.0, n_eval=1 << 22, sha
         blob, rep = ctx.train(rs, train_h, N=width, blocks=blocks, batch=8192, epochs=1000, max_rounds=1, alpha=100,
                               holdout=0.05, time_budget_s=train_s, seed=73)
         ctx.load_model(rs, blob)
-        path = "fused_bf16" if width == 512 else "plain_fp32"
+        path = "fused_bf16" if width in (256, 512) else "plain_fp32"
         st = ctx.classify(rs, d, ids, path=path, stats=True)
         ctx.classify(rs, d, ids, path=path, paper=True)
         paper_acc = float((ids == exact).float().mean().item())
-        reps = 5 if width == 512 else 1
+        reps = 5 if path == "fused_bf16" else 1
         for _ in range(2):
             ctx.classify(rs, d, ids, path=path, graph=True)
         torch.cuda.synchronize()

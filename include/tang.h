@@ -156,10 +156,10 @@ typedef struct tang_model_header {
 
 /* Validate and upload a model for ruleset `rs`; keeps an FP32 copy and derives the BF16 and
  * (if calibrated) FP8 copies. Requires C == n_tuples, S == 7. The tensor-core paths further
- * require N == 512 and 1 <= blocks <= 31 (other shapes use the FP32 path only); the default
- * N=256 kernel takes any C (its output layer runs in 256-column chunks), the N=128 variants
- * (TANG_FUSED_1SM, _2SM, _MCAST2/4) serve only blocks == 6 and C <= 128, and other models always
- * run the N=256 kernel.
+ * require N == 256 or 512 and 1 <= blocks <= 31 (other shapes use the FP32 path only); the
+ * default N=256 kernel takes any C (its output layer runs in 256-column chunks), the N=128
+ * variants (TANG_FUSED_1SM, _2SM, _MCAST2/4) serve only N == 512, blocks == 6 and C <= 128, and
+ * other models always run the N=256 kernel.
  * Replaces a previous model of the ruleset. Synchronous: waits for all work on the device.
  * Hot swap (§5.2.2 deploys retrained weights while classification goes on): when the previous
  * model has the same S, N, blocks, C and FP8 calibration state, the new weights are written into

@@ -385,7 +385,7 @@ int tang_load_model(tang_ctx *ctx, uint32_t rsh, const void *blob, size_t bytes)
     m->Wc = p;
     p += size_t(N) * hd.C;
     m->bc = p;
-    if (N == 512) {  // tensor-core copies (tc_prepare_model checks the remaining limits)
+    if (N == 512 || N == 256) {  // tensor-core copies (tc_prepare_model checks the remaining limits)
         rc = tc_prepare_model(ctx, *m);
         if (rc) {
             tang_model_free(ctx, m.get());
@@ -411,7 +411,7 @@ static int run_infer(tang_ctx *ctx, Ruleset &rs, const tang_header *h, uint32_t 
                      int precision, cudaStream_t st, int variant = 0) {
     if (!rs.model) return set_err(ctx, TANG_EINVAL, "ruleset %u has no model", rs.handle);
     if (precision == TANG_FP32) return mlp_fp32_forward(ctx, *rs.model, h, n, logits, tuple, st);
-    if (!rs.model->d_wbf16) return set_err(ctx, TANG_EUNSUPPORTED, "tensor-core path needs N == 512 and 1 <= blocks <= 31");
+    if (!rs.model->d_wbf16) return set_err(ctx, TANG_EUNSUPPORTED, "tensor-core path needs N == 256 or 512 and 1 <= blocks <= 31");
     if (precision == TANG_FP8 && !rs.model->has_fp8)
         return set_err(ctx, TANG_EINVAL, "FP8 path needs a calibrated model (act_amax)");
     const TuneEntry *tune = nullptr;
@@ -463,7 +463,7 @@ static int enqueue_classify(tang_ctx *ctx, Ruleset &rs, const tang_header *h, ui
         case TANG_PATH_FUSED_BF16:
         case TANG_PATH_FUSED_FP8: {
             if (!rs.model) return set_err(ctx, TANG_EINVAL, "ruleset %u has no model", rs.handle);
-            if (!rs.model->d_wbf16) return set_err(ctx, TANG_EUNSUPPORTED, "tensor-core path needs N == 512 and 1 <= blocks <= 31");
+            if (!rs.model->d_wbf16) return set_err(ctx, TANG_EUNSUPPORTED, "tensor-core path needs N == 256 or 512 and 1 <= blocks <= 31");
             const int prec = path == TANG_PATH_FUSED_BF16 ? TANG_BF16 : TANG_FP8;
             if (prec == TANG_FP8 && !rs.model->has_fp8)
                 return set_err(ctx, TANG_EINVAL, "FP8 path needs a calibrated model (act_amax)");

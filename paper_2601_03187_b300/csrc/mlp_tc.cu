@@ -599,12 +599,11 @@ int make_tmap(tang_ctx *ctx, CUtensorMap *m, void *base, uint32_t rows, bool f8,
 // per-output-channel scales, FP32 biases, FP8 dequantisation factors and activation scales.
 int tc_prepare_model(tang_ctx *ctx, DeviceModel &m) {
     const uint32_t N = m.N, C = m.C;
-    // the tensor-core kernels are built for N = 512; the N=256 kernel takes any block count up to
-    // 31 (the N=128 variants only the paper's 6)
-    if (N != 512 || m.blocks < 1 || m.blocks > 31) return TANG_OK;
-    // the N=128 variants take up to 128 classes; the N=256 kernel any count, in 256-row output
-    // tiles (padded with zero rows past Cpad)
-    const bool narrow = C <= 128;
+    // the N=256 kernel takes width 256 or 512, any block count up to 31 and any class count (in
+    // 256-row output tiles, padded with zero rows past Cpad); the N=128 variants only width 512,
+    // the paper's 6 blocks and up to 128 classes
+    if ((N != 512 && N != 256) || m.blocks < 1 || m.blocks > 31) return TANG_OK;
+    const bool narrow = C <= 128 && N == 512;
     const int nl = int(2 * m.blocks);  // N x N layers
     m.layers = uint32_t(nl);
     const uint32_t Cpad = m.Cpad;  // multiple of 32
@@ -804,8 +803,8 @@ int tc_launch(tang_ctx *ctx, Ruleset &rs, const tang_header *h, uint32_t n, uint
     prm.trace = d_trace;
 #endif
     int v = variant ? variant : (tune && tune->fused_variant ? tune->fused_variant : kDefaultVariant);
-    // the N=128 variants are built for 6 blocks and at most 128 classes
-    const bool narrow6 = m.layers == uint32_t(tc::kLayers) && m.C <= 128;
+    // the N=128 variants are built for width 512, 6 blocks and at most 128 classes
+    const bool narrow6 = m.N == 512 && m.layers == uint32_t(tc::kLayers) && m.C <= 128;
     if (!narrow6) v = 5;
     if (v == 2 || v == 5) {
         const int rc = v == 2 ? tc2_launch(ctx, m, prm, f8, st, tune ? tune->fused_grid : 0)

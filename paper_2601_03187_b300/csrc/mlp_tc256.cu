@@ -42,7 +42,6 @@ namespace tang {
 
 namespace tc256 {
 constexpr int kM = 128;
-constexpr int kHid = 512;
 constexpr int kStageBytes = 32768;  // 256 rows x 128 bytes
 constexpr int kNumEpiWarps = 16;
 // Warp groups (4 warps each): 0 = producer (warp 0) and MMA issuer (warp 1); 1..4 = the epilogue;
@@ -66,19 +65,19 @@ constexpr int kArgG = 3;
 // Shared memory: u (the FC1 output as swizzled K-blocks of 128 rows x 128 bytes; its first 16 KB
 // also hold the next tile's layer-0 operand between the last FC2 and the next FC1 epilogue), the
 // weight stages, the predicted-tuple handoff to the search warps, the barriers, the partial argmax.
-template <bool F8>
+template <bool F8, int HID>
 struct Layout {
     static constexpr int kStages = F8 ? 4 : 3;
-    static constexpr int kYBytes = kM * kHid * (F8 ? 1 : 2);
+    static constexpr int kYBytes = kM * HID * (F8 ? 1 : 2);
     static constexpr int kOffStage = kYBytes;
     static constexpr int kOffTidx = kOffStage + kStages * kStageBytes;
     static constexpr int kOffBar = kOffTidx + 2 * kM * 4;
     static constexpr int kNumBars = 2 * kStages + 1 + 1 + 8 + 2 + 2 + 1 + 1 + 1;
     static constexpr int kOffMisc = kOffBar + kNumBars * 8;
     // per-row partial argmax of the four column groups ([4][128] floats, then [4][128] ints): in
-    // the u buffer's second half for BF16 (idle from the last FC2 to the next tile's FC1 chunk 1),
-    // in a region of its own for FP8
-    static constexpr int kOffPart = F8 ? kOffMisc + 16 : 65536;
+    // the u buffer's second half for BF16 (idle from the last FC2 to the next tile's FC1 epilogue
+    // that writes it), in a region of its own for FP8
+    static constexpr int kOffPart = F8 ? kOffMisc + 16 : kYBytes / 2;
     static constexpr int kSmemBytes = (F8 ? kOffPart + 4096 : kOffMisc + 16) + 1024;  // + slack to align the base
     static_assert(kSmemBytes <= 232448, "exceeds the 227 KB of shared memory per CTA");
 };
@@ -86,12 +85,12 @@ struct Layout {
 
 // 24 warps, launched at 80 registers per thread (6 x 32 x 80 = 15,360 of a sub-partition's 16K);
 // after setup the control group drops to 40, the search group to 56 and the epilogue rises to 96.
-template <bool F8>
+template <bool F8, int HID>
 __global__ void __launch_bounds__(tc256::kThreads, 1)
     k_tc256_classify(const __grid_constant__ CUtensorMap tm_hid, const __grid_constant__ CUtensorMap tm_out,
                      const __grid_constant__ CUtensorMap tm_l0, const TcParams p) {
     using namespace tc256;
-    using Lay = Layout<F8>;
+    using Lay = Layout<F8, HID>;
     constexpr int kStages = Lay::kStages;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -115,8 +114,9 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
     // to whole 256-row tiles when Cpad > 256, so every tile load is in bounds)
     const int n_oc = int((p.Cpad + 255) >> 8);
     const uint32_t out_box = p.Cpad < 256 ? p.Cpad : 256u;
-    constexpr int KB = F8 ? 4 : 8;
-    constexpr int KBW = F8 ? 128 : 64;
+    constexpr int KBW = F8 ? 128 : 64;  // K per weight stage: 128 bytes of a row
+    constexpr int KB = HID / KBW;       // K-blocks per layer
+    constexpr int NCH = HID / 256;      // 256-column chunks per layer
     constexpr uint32_t kActArrivals = F8 ? 8 : 4;  // 64-column units per K-block x 4 lane quadrants
 
     if (threadIdx.x == 0) {
@@ -180,8 +180,8 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
                 }
             };
             for (uint32_t tile = blockIdx.x; tile < p.n_tiles && ok; tile += gridDim.x) {
-                // layer 0: two 256-row chunks of the [512][64] BF16 operand, one stage each
-                for (int c = 0; c < 2 && ok; ++c) {
+                // layer 0: the 256-row chunks of the [HID][64] BF16 operand, one stage each
+                for (int c = 0; c < NCH && ok; ++c) {
                     uint8_t *dst = next_stage();
                     if (!dst) break;
                     ptx::mbar_arrive_expect_tx(&full[stage], kStageBytes);
@@ -189,14 +189,14 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
                     advance();
                 }
                 for (int L = 0; L <= nl && ok; ++L) {
-                    const int nch = L == nl ? n_oc : 2;
+                    const int nch = L == nl ? n_oc : NCH;
                     for (int c = 0; c < nch && ok; ++c)
                         for (int kb = 0; kb < KB; ++kb) {
                             uint8_t *dst = next_stage();
                             if (!dst) break;
                             if (L < nl) {
                                 ptx::mbar_arrive_expect_tx(&full[stage], kStageBytes);
-                                ptx::tma_load_2d(dst, &tm_hid, &full[stage], kb * KBW, L * kHid + c * 256);
+                                ptx::tma_load_2d(dst, &tm_hid, &full[stage], kb * KBW, L * HID + c * 256);
                             } else {
                                 ptx::mbar_arrive_expect_tx(&full[stage], out_box * 128);
                                 ptx::tma_load_2d(dst, &tm_out, &full[stage], kb * KBW, c * 256);
@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
             int err = 0;
             for (uint32_t tile = blockIdx.x; tile < p.n_tiles && !err; tile += gridDim.x, ++ntile) {
                 // ---- layer 0: A = the header bytes (shared memory), B = the split weights
-                for (int c = 0; c < 2; ++c, ++uses) {
+                for (int c = 0; c < NCH; ++c, ++uses) {
                     TC_TRACE(trace::kMma + uses * 12 + 0, uses < uint32_t(trace::kChunks));
                     if (uses > 0 && !ptx::mbar_wait(acc_empty, (uses - 1) & 1, sAbort, kTimeoutNs)) {
                         err = 2;
@@ -254,7 +254,7 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
                 }
                 for (int L = 0; L <= nl && !err; ++L, ++lay) {
                     const bool a_tmem = (L & 1) == 0;  // FC1 and the output layer read x from TMEM
-                    const int nch = L == nl ? n_oc : 2;
+                    const int nch = L == nl ? n_oc : NCH;
                     for (int c = 0; c < nch && !err; ++c, ++uses) {
                         const uint32_t idesc =
                             L == nl ? ptx::idesc_make(128, p.Cpad - 256u * c < 256u ? p.Cpad - 256u * c : 256u, F8) : idesc_h;
@@ -406,10 +406,10 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
         };
         auto load_cc = [&](int L, int c) -> ColConst {
             const int col = (4 * c + g) * 64 + lane;
-            const float *bv = F8 ? p.fold8 + size_t(nl + L) * kHid : p.bias + size_t(L) * kHid;
+            const float *bv = F8 ? p.fold8 + size_t(nl + L) * HID : p.bias + size_t(L) * HID;
             ColConst r{__ldg(bv + col), __ldg(bv + col + 32), 0.f, 0.f};
             if (F8) {
-                const float *dv = p.fold8 + size_t(L) * kHid;
+                const float *dv = p.fold8 + size_t(L) * HID;
                 r.d0 = __ldg(dv + col);
                 r.d1 = __ldg(dv + col + 32);
             }
@@ -420,7 +420,7 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
         for (uint32_t tile = blockIdx.x; tile < p.n_tiles && ok; tile += gridDim.x) {
             const uint32_t i = tile * kM + r;
             // ---- layer 0 from the accumulator (bias included): units 4c+g of x
-            for (int c = 0; c < 2; ++c, ++uses) {
+            for (int c = 0; c < NCH; ++c, ++uses) {
                 if (!ptx::mbar_wait(acc_full, uses & 1, sAbort, kTimeoutNs)) {
                     fail(16);
                     ok = false;
@@ -447,14 +447,14 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
                 // BF16: v = acc + b. FP8: v = acc * (dq * s_out) + b * s_out, in the output's units.
                 // FP8 residual: x is stored in the units of its own layer input (scale s[L-1])
                 const float rr = F8 && fc2 ? sa[L + 1] / sa[L - 1] : 1.f;
-                for (int c = 0; c < 2; ++c, ++uses) {
+                for (int c = 0; c < NCH; ++c, ++uses) {
                     [[maybe_unused]] const bool tr = lane == 0 && q == 2 && g < 2 && uses < uint32_t(trace::kChunks);
                     [[maybe_unused]] const int tslot = trace::kEpi + (g * trace::kChunks + int(uses)) * 4;
                     TC_TRACE(tslot + 0, tr);
                     const int unit = 4 * c + g;
                     // this chunk's column constants, loaded one chunk ago; now the next chunk's
                     const ColConst cc = next_cc;
-                    next_cc = load_cc(c == 0 ? L : (L + 1 < nl ? L + 1 : 0), c ^ 1);
+                    next_cc = c + 1 < NCH ? load_cc(L, c + 1) : load_cc(L + 1 < nl ? L + 1 : 0, 0);
                     if (!ptx::mbar_wait(acc_full, uses & 1, sAbort, kTimeoutNs)) {
                         fail(16);
                         ok = false;
@@ -520,7 +520,7 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
                     TC_TRACE(tslot + 3, tr);
                     // after the last FC2 chunk (its MMAs, the last readers of u, have completed):
                     // the next tile's layer-0 operand
-                    if (L == nl - 1 && c == 1 && g == 0 && tile + gridDim.x < p.n_tiles) write_features(tile + gridDim.x);
+                    if (L == nl - 1 && c == NCH - 1 && g == 0 && tile + gridDim.x < p.n_tiles) write_features(tile + gridDim.x);
                 }
             }
             if (!ok) break;
@@ -530,8 +530,8 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
             {
                 float best = -INFINITY;
                 int arg = 0;
-                const float *bias = p.bias + nl * kHid;
-                const float *dq = F8 ? p.dq + nl * kHid : nullptr;
+                const float *bias = p.bias + nl * HID;
+                const float *dq = F8 ? p.dq + nl * HID : nullptr;
                 for (int oc = 0; oc < n_oc; ++oc) {
                     if (!ptx::mbar_wait(acc_full, uses & 1, sAbort, kTimeoutNs)) {
                         fail(32);
@@ -675,22 +675,22 @@ struct Tc256Maps {
 // Round to the nearest BF16 value, as a float.
 float bf16_round_host(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 
-// The layer-0 operand B[n][k] (n < 512, k < 64) with sum_k A[k] B[n][k] = s * (b0[n] + sum_t
+// The layer-0 operand B[n][k] (n < N, k < 64) with sum_k A[k] B[n][k] = s * (b0[n] + sum_t
 // f_t W0[t][n]) for A = [hi(7), lo(7)] x 3, 1 x 3, 0 x 19 (f_t = 256 hi_t + lo_t): the weight
 // parts scaled by 256 meet the high bytes, the plain parts the low bytes.
-void layer0_operand(const float *W0, const float *b0, float s, __nv_bfloat16 *B) {
+void layer0_operand(const float *W0, const float *b0, uint32_t N, float s, __nv_bfloat16 *B) {
     auto split = [](float w, float part[3]) {
         part[0] = bf16_round_host(w);
         const float r1 = w - part[0];  // exact in FP32
         part[1] = bf16_round_host(r1);
         part[2] = bf16_round_host(r1 - part[1]);
     };
-    for (uint32_t n = 0; n < 512; ++n) {
+    for (uint32_t n = 0; n < N; ++n) {
         __nv_bfloat16 *row = B + size_t(n) * tc256::kL0K;
         for (int k = 0; k < tc256::kL0K; ++k) row[k] = __float2bfloat16_rn(0.f);
         for (int t = 0; t < 7; ++t) {
             float part[3];
-            split(W0[size_t(t) * 512 + n] * s, part);
+            split(W0[size_t(t) * N + n] * s, part);
             for (int pi = 0; pi < 3; ++pi) {
                 row[pi * 14 + t] = __float2bfloat16_rn(part[pi] * 256.f);
                 row[pi * 14 + 7 + t] = __float2bfloat16_rn(part[pi]);
@@ -704,51 +704,54 @@ void layer0_operand(const float *W0, const float *b0, float s, __nv_bfloat16 *B)
 }  // namespace
 
 // 256-row hidden-layer maps, output-layer maps of up to 256-row tiles, and the layer-0 operands
-// with their maps.
+// with their maps, for width N = 256 or 512.
 int tc256_prepare_model(tang_ctx *ctx, DeviceModel &m) {
-    if (!m.d_wbf16) return TANG_OK;
+    if (!m.d_wbf16 || (m.N != 256 && m.N != 512)) return TANG_OK;
     Tc256Maps *maps = static_cast<Tc256Maps *>(aligned_alloc(64, 2 * sizeof(Tc256Maps)));
     m.tmap256 = maps;
-    const float *W0 = m.host_params.data(), *b0 = W0 + size_t(7) * m.N;
-    std::vector<__nv_bfloat16> l0(size_t(2) * 512 * tc256::kL0K);
-    layer0_operand(W0, b0, 1.f, l0.data());
-    if (m.has_fp8) layer0_operand(W0, b0, m.act_scale[0], l0.data() + size_t(512) * tc256::kL0K);
+    const uint32_t N = m.N;
+    const float *W0 = m.host_params.data(), *b0 = W0 + size_t(7) * N;
+    std::vector<__nv_bfloat16> l0(size_t(2) * N * tc256::kL0K);
+    layer0_operand(W0, b0, N, 1.f, l0.data());
+    if (m.has_fp8) layer0_operand(W0, b0, N, m.act_scale[0], l0.data() + size_t(N) * tc256::kL0K);
     int rc = ctx_alloc(ctx, l0.size() * 2, &m.d_l0);
     if (rc) return rc;
     cudaMemcpy(m.d_l0, l0.data(), l0.size() * 2, cudaMemcpyHostToDevice);
     // output tiles of min(Cpad, 256) rows; past 256 the copies hold whole 256-row tiles
     const size_t hid = size_t(m.layers) * m.N * m.N;
     const uint32_t out_rows = m.Cpad <= 256 ? m.Cpad : (m.Cpad + 255) / 256 * 256, out_box = std::min<uint32_t>(m.Cpad, 256);
-    if ((rc = make_tmap(ctx, &maps[0].out, static_cast<__nv_bfloat16 *>(m.d_wbf16) + hid, out_rows, false, out_box))) return rc;
-    if ((rc = make_tmap(ctx, &maps[0].hid, m.d_wbf16, m.layers * m.N, false, 256))) return rc;
-    if ((rc = make_tmap(ctx, &maps[0].l0, m.d_l0, 512, false, 256, tc256::kL0K))) return rc;
+    if ((rc = make_tmap(ctx, &maps[0].out, static_cast<__nv_bfloat16 *>(m.d_wbf16) + hid, out_rows, false, out_box, N)))
+        return rc;
+    if ((rc = make_tmap(ctx, &maps[0].hid, m.d_wbf16, m.layers * N, false, 256, N))) return rc;
+    if ((rc = make_tmap(ctx, &maps[0].l0, m.d_l0, N, false, 256, tc256::kL0K))) return rc;
     if (m.d_wfp8) {
-        if ((rc = make_tmap(ctx, &maps[1].out, static_cast<uint8_t *>(m.d_wfp8) + hid, out_rows, true, out_box))) return rc;
-        if ((rc = make_tmap(ctx, &maps[1].hid, m.d_wfp8, m.layers * m.N, true, 256))) return rc;
-        rc = make_tmap(ctx, &maps[1].l0, static_cast<__nv_bfloat16 *>(m.d_l0) + size_t(512) * tc256::kL0K, 512, false,
-                       256, tc256::kL0K);
+        if ((rc = make_tmap(ctx, &maps[1].out, static_cast<uint8_t *>(m.d_wfp8) + hid, out_rows, true, out_box, N)))
+            return rc;
+        if ((rc = make_tmap(ctx, &maps[1].hid, m.d_wfp8, m.layers * N, true, 256, N))) return rc;
+        rc = make_tmap(ctx, &maps[1].l0, static_cast<__nv_bfloat16 *>(m.d_l0) + size_t(N) * tc256::kL0K, N, false, 256,
+                       tc256::kL0K);
     }
     return rc;
 }
 
-template <bool F8>
+template <bool F8, int HID>
 static int tc256_launch_t(tang_ctx *ctx, const Tc256Maps &maps, const TcParams &prm, cudaStream_t st, uint32_t grid) {
-    constexpr int kSmem = tc256::Layout<F8>::kSmemBytes;
+    constexpr int kSmem = tc256::Layout<F8, HID>::kSmemBytes;
     static bool attr_done = false;
     if (!attr_done) {
         // the setmaxnreg split assumes the launch register count it was sized for: with any other
         // count an increase could wait forever, so refuse to launch
         cudaFuncAttributes fa{};
-        cudaError_t e = cudaFuncGetAttributes(&fa, k_tc256_classify<F8>);
+        cudaError_t e = cudaFuncGetAttributes(&fa, k_tc256_classify<F8, HID>);
         if (e != cudaSuccess) return set_err(ctx, TANG_EDEVICE, "N=256 kernel attributes: %s", cudaGetErrorString(e));
         if (fa.numRegs != tc256::kRegLaunch)
             return set_err(ctx, TANG_EDEVICE, "N=256 kernel built with %d registers per thread, expected %d", fa.numRegs,
                            tc256::kRegLaunch);
-        e = cudaFuncSetAttribute(k_tc256_classify<F8>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+        e = cudaFuncSetAttribute(k_tc256_classify<F8, HID>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
         if (e != cudaSuccess) return set_err(ctx, TANG_EDEVICE, "smem attribute (N=256): %s", cudaGetErrorString(e));
         attr_done = true;
     }
-    k_tc256_classify<F8><<<grid, tc256::kThreads, kSmem, st>>>(maps.hid, maps.out, maps.l0, prm);
+    k_tc256_classify<F8, HID><<<grid, tc256::kThreads, kSmem, st>>>(maps.hid, maps.out, maps.l0, prm);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return set_err(ctx, TANG_EDEVICE, "N=256 kernel launch: %s", cudaGetErrorString(e));
     return TANG_OK;
@@ -766,7 +769,10 @@ int tc256_launch(tang_ctx *ctx, DeviceModel &m, const TcParams &prm, bool f8, cu
     cudaMemsetAsync(d_trace, 0, sizeof(unsigned long long) * trace::kTotal, st);
     prm_t.trace = d_trace;
 #endif
-    const int rc = f8 ? tc256_launch_t<true>(ctx, maps, prm_t, st, grid) : tc256_launch_t<false>(ctx, maps, prm_t, st, grid);
+    const int rc = m.N == 512 ? (f8 ? tc256_launch_t<true, 512>(ctx, maps, prm_t, st, grid)
+                                    : tc256_launch_t<false, 512>(ctx, maps, prm_t, st, grid))
+                              : (f8 ? tc256_launch_t<true, 256>(ctx, maps, prm_t, st, grid)
+                                    : tc256_launch_t<false, 256>(ctx, maps, prm_t, st, grid));
     if (rc) return rc;
 #ifdef TANG_TC_TRACE
     if (const char *path = getenv("TANG_TC_TRACE_FILE")) {

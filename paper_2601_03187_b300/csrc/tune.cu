@@ -44,7 +44,7 @@ extern "C" int tang_autotune(tang_ctx *ctx, uint32_t rsh, const tang_header *d_h
             e.fused_grid = g;
             cands.push_back(e);
         }
-        if (rs.model->layers == 12 && rs.model->C <= 128)  // the N=128 variants' limits
+        if (rs.model->N == 512 && rs.model->layers == 12 && rs.model->C <= 128)  // the N=128 variants' limits
             for (int v : {1, 2, 3, 4}) {
                 TuneEntry e;
                 e.fused_variant = v;

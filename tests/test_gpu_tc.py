@@ -141,16 +141,17 @@ def test_predictions_agree_across_precisions(setup):
     assert (tv == t16).mean() > 0.998
 
 
-@pytest.mark.parametrize("blocks", [1, 2, 3])
-def test_other_depths_on_the_n256_kernel(blocks):
-    """Networks of 1-3 residual blocks (the model-size sweep) run on the N=256 kernel: logits
-    within the bound of the float64 forward of the quantised weights (BF16 and FP8), rule ids
-    exact; the N=128 variants, built for 6 blocks, are not used for them."""
+@pytest.mark.parametrize("width,blocks", [(512, 1), (512, 2), (512, 3), (256, 1), (256, 2), (256, 6)])
+def test_other_shapes_on_the_n256_kernel(width, blocks):
+    """Networks of 1-3 residual blocks at width 512, and of width 256 (one 256-column chunk per
+    layer), run on the N=256 kernel: logits within the bound of the float64 forward of the
+    quantised weights (BF16 and FP8), rule ids exact; the N=128 variants, built for width 512 and
+    6 blocks, are not used for them."""
     ctx = tg.Context(0)
     rules = wl.rules_for_config(0)
     rs = ctx.load_ruleset(rules)
     T = ctx.ruleset_info(rs)["n_tuples"]
-    p = random_params(np.random.default_rng(100 + blocks), N=512, blocks=blocks, C=T)
+    p = random_params(np.random.default_rng(100 + blocks + width), N=width, blocks=blocks, C=T)
     h = wl.trace_for_config(0, rules, seed=9)[:20000 + 3]
     X = mlp.features(h[:4096])
     p64 = {k: ([a.astype(np.float64) for a in v] if isinstance(v, list) else v.astype(np.float64)) for k, v in p.items()}
@@ -163,7 +164,7 @@ def test_other_depths_on_the_n256_kernel(blocks):
     for prec in ("bf16", "fp8"):
         q = bf16_weights(p64) if prec == "bf16" else e4m3_weights(p64)
         z64 = mlp.forward(q, X)
-        for variant in (None, "1sm"):  # "1sm" falls back to the N=256 kernel for these depths
+        for variant in (None, "1sm"):  # "1sm" falls back to the N=256 kernel for these shapes
             z, tup = infer(ctx, rs, h[:4096], T, tg.BF16 if prec == "bf16" else tg.FP8, variant)
             tol = logit_tolerance(q, X, U32, U_BF16 if prec == "bf16" else U_E4M3)
             assert np.isfinite(z).all()
