@@ -191,18 +191,19 @@ def _spread_rules(n, seed):
     return rules
 
 
-@pytest.mark.parametrize("n_rules", [200, 350, 1500])
-def test_many_tuples_on_the_n256_kernel(n_rules):
+@pytest.mark.parametrize("n_rules,width", [(200, 512), (350, 512), (1500, 512), (350, 256)])
+def test_many_tuples_on_the_n256_kernel(n_rules, width):
     """Rulesets with 187, 308 and 824 tuples on the N=256 kernel, whose output layer then runs
     as one chunk of 192 columns, as 256 + 64, and as three of 256 + 64: logits within the bound
-    of the float64 forward of the quantised weights, argmax = the first maximum, ids exact."""
+    of the float64 forward of the quantised weights, argmax = the first maximum, ids exact (and
+    the 308-tuple case at width 256)."""
     ctx = tg.Context(0)
     rules = _spread_rules(n_rules, 300 + n_rules)
     rs = ctx.load_ruleset(rules)
     T = ctx.ruleset_info(rs)["n_tuples"]
     assert T == {200: 187, 350: 308, 1500: 824}[n_rules], T
     blocks = 2
-    p = random_params(np.random.default_rng(n_rules), N=512, blocks=blocks, C=T)
+    p = random_params(np.random.default_rng(n_rules + width), N=width, blocks=blocks, C=T)
     h = wl.gen_trace(rules, [("inside", 9000), ("random", 1000)], 31)
     X = mlp.features(h[:4096])
     p64 = {k: ([a.astype(np.float64) for a in v] if isinstance(v, list) else v.astype(np.float64)) for k, v in p.items()}
