@@ -661,6 +661,15 @@ def main():
     extra = {}
     # the secondary measurements characterise one GPU: they run at N = 1 only (the timed headline
     # and e2e run on every rank)
+    if world == 1:
+        # the search alone (every tuple probed in best-priority order with early exit): the gather
+        # kernel's own rate, also in --quick runs so that a short command profiles it
+        dtn = time_path("no_nn", args.steps, args.warmup)
+        extra["no_nn_mpkts"] = round(n * args.steps / dtn / 1e6, 3)
+        st_no = ctx.classify(rs, d_h, ids, path="no_nn", stats=True)
+        extra["no_nn_ids_equal_fused"] = bool((ids.cpu().numpy().view(np.uint32) == ids_fused).all())
+        extra["no_nn_probes_per_pkt"] = round(st_no["probes"] / n, 4)
+        extra["no_nn_rule_reads_per_pkt"] = round(st_no["rule_reads"] / n, 4)
     if not args.quick and world == 1:
         dt8 = time_path("fused_fp8", args.steps, args.warmup)
         extra["fused_fp8_mpkts"] = round(n * args.steps / dt8 / 1e6, 3)
@@ -670,12 +679,6 @@ def main():
         dtp = time_path("plain_fp32", 2, 1)
         extra["plain_fp32_mpkts"] = round(n * 2 / dtp / 1e6, 3)
         extra["plain_ids_equal_fused"] = bool((ids.cpu().numpy().view(np.uint32) == ids_fused).all())
-        dtn = time_path("no_nn", args.steps, args.warmup)
-        extra["no_nn_mpkts"] = round(n * args.steps / dtn / 1e6, 3)
-        st_no = ctx.classify(rs, d_h, ids, path="no_nn", stats=True)
-        extra["no_nn_ids_equal_fused"] = bool((ids.cpu().numpy().view(np.uint32) == ids_fused).all())
-        extra["no_nn_probes_per_pkt"] = round(st_no["probes"] / n, 4)
-        extra["no_nn_rule_reads_per_pkt"] = round(st_no["rule_reads"] / n, 4)
 
         # latency per classify call (device-resident), fused vs plain
         lat = {}
