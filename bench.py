@@ -52,11 +52,18 @@ KERNEL_SOURCES = [os.path.join(ROOT, "paper_2601_03187_b300", "csrc", f)
 
 
 def kernel_digest():
+    """sha256 of the fused kernel's code: its sources with comments removed and whitespace runs
+    collapsed, so that an edit to a comment keeps the profiled figures valid and any code edit
+    does not."""
     import hashlib
+    import re
+    token = re.compile(r'"(?:\\.|[^"\\])*"|//[^\n]*|/\*.*?\*/', re.S)
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
-        with open(f, "rb") as fh:
-            h.update(fh.read())
+        with open(f) as fh:
+            src = fh.read()
+        code = token.sub(lambda m: m.group(0) if m.group(0).startswith('"') else " ", src)
+        h.update(" ".join(code.split()).encode())
     return h.hexdigest()
 
 

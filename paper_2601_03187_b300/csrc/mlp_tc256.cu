@@ -9,12 +9,14 @@
 // release the accumulator at once; bias, residual, ReLU, quantisation and the operand stores
 // then overlap the next chunk's MMAs.
 //
-// Per tile (128 packets): layer 0 on the tensor core -> x (TMEM); per block: FC1 in two
-// 256-column chunks (A = x from TMEM) -> u (swizzled shared memory); FC2 in two chunks (A = u
-// from shared memory) -> x = ReLU(acc + b2 + x) in place (Eq. 1); output FC (N = Cpad) + argmax;
-// the exact search of §5.1.1 on 4 search warps.
+// Per tile (128 packets), for the paper's width 512: layer 0 on the tensor core -> x (TMEM); per
+// block: FC1 in two 256-column chunks (A = x from TMEM) -> u (swizzled shared memory); FC2 in two
+// chunks (A = u from shared memory) -> x = ReLU(acc + b2 + x) in place (Eq. 1); output FC in
+// 256-column chunks (any tuple count) + argmax; the exact search of §5.1.1 on 4 search warps.
+// The width is a template parameter: at 256 every layer is one chunk and u and x take half the
+// space.
 //
-// Layer 0 (7 header fields -> 512, FP32 in the other kernels) is one K=48 BF16 contraction per
+// Layer 0 (7 header fields -> width, FP32 in the other kernels) is one K=48 BF16 contraction per
 // 256 columns with FP32 accumulation: every 16-bit field f splits exactly into bytes,
 // f = 256 * hi + lo, and every weight and bias into three BF16 parts w1 + w2 + w3 that carry its
 // 24 significant bits, so A = [hi(7), lo(7)] x 3 parts, 1 x 3 bias parts, and all products are
@@ -441,7 +443,7 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
                 act_arrive(unit * 64);
             }
             if (!ok) break;
-            // ---- hidden layers, two 256-column chunks each
+            // ---- hidden layers, NCH 256-column chunks each
             for (int L = 0; L < nl && ok; ++L) {
                 const bool fc2 = (L & 1) != 0;
                 // BF16: v = acc + b. FP8: v = acc * (dq * s_out) + b * s_out, in the output's units.
