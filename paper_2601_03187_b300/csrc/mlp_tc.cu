@@ -664,19 +664,29 @@ int tc_prepare_model(tang_ctx *ctx, DeviceModel &m) {
         }
         std::vector<uint8_t> w8(hid + rows_out * N, 0);
         std::vector<float> dq(size_t(nl) * N + Cpad, 0.f);
-        auto quant_col = [&](const float *Wsrc, uint32_t ncols, uint32_t n, size_t dst_row, float sa, float *dq_out) {
-            float amax = 0.f;
-            for (uint32_t k = 0; k < N; ++k) amax = std::max(amax, std::fabs(Wsrc[size_t(k) * ncols + n]));
+        // Weight scales: one per hidden layer, 448 / max |W_l| (a single dequantisation factor for
+        // the whole layer, so the fused kernel's epilogue needs no per-column scale); one per
+        // output column for the output layer, 448 / max |Wc[:, c]|.
+        auto amax_of = [&](const float *Wsrc, uint32_t ncols, uint32_t c0, uint32_t c1) {
+            float a = 0.f;
+            for (uint32_t k = 0; k < N; ++k)
+                for (uint32_t n = c0; n < c1; ++n) a = std::max(a, std::fabs(Wsrc[size_t(k) * ncols + n]));
+            return a;
+        };
+        auto quant_col = [&](const float *Wsrc, uint32_t ncols, uint32_t n, size_t dst_row, float sa, float amax,
+                             float *dq_out) {
             const float sw = amax > 0.f ? 448.0f / amax : 1.0f;
             for (uint32_t k = 0; k < N; ++k)
                 w8[dst_row * N + k] = __nv_cvt_float_to_fp8(Wsrc[size_t(k) * ncols + n] * sw, __NV_SATFINITE, __NV_E4M3);
             *dq_out = 1.0f / (sa * sw);
         };
-        for (int l = 0; l < nl; ++l)
+        for (int l = 0; l < nl; ++l) {
+            const float amax = amax_of(W[l], N, 0, N);
             for (uint32_t n = 0; n < N; ++n)
-                quant_col(W[l], N, n, size_t(l) * N + n, m.act_scale[l], &dq[size_t(l) * N + n]);
+                quant_col(W[l], N, n, size_t(l) * N + n, m.act_scale[l], amax, &dq[size_t(l) * N + n]);
+        }
         for (uint32_t c = 0; c < C; ++c)
-            quant_col(Wc, C, c, hid / N + c, m.act_scale[nl], &dq[size_t(nl) * N + c]);
+            quant_col(Wc, C, c, hid / N + c, m.act_scale[nl], amax_of(Wc, C, c, c + 1), &dq[size_t(nl) * N + c]);
         rc = ctx_alloc(ctx, w8.size(), &m.d_wfp8);
         if (!rc) rc = ctx_alloc(ctx, (dq.size() + nl + 1) * 4, (void **)&m.d_wscale8);
         if (rc) return rc;

@@ -396,26 +396,21 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
             if (lane == 0) ptx::mbar_arrive(feat_full);
         };
 
-        // Per-column constants of the hidden layers, one per lane: the bias (FP8: b * s_out) and,
-        // for FP8, the scale dq * s_out of columns unit * 64 + lane and unit * 64 + 32 + lane.
+        // Per-column constants of the hidden layers, one per lane: the bias (FP8: b * s_out) of
+        // columns unit * 64 + lane and unit * 64 + 32 + lane; for FP8 also the layer's scale
+        // dq * s_out, the same for every column (the hidden layers have one weight scale each).
         // Shuffles broadcast them across the warp's rows. They are loaded one chunk ahead: loads
         // issued at the chunk's start stalled the FP8 epilogue, which runs behind the MMAs and so
         // finds its accumulator ready, for an L2 round trip; broadcast loads of whole lines missed
         // the small L1 left beside 231 KB of shared memory in both precisions (about 1k cycles per
         // chunk); broadcast reads from a shared-memory copy were no faster than the shuffles.
         struct ColConst {
-            float b0, b1, d0, d1;
+            float b0, b1, d;
         };
         auto load_cc = [&](int L, int c) -> ColConst {
             const int col = (4 * c + g) * 64 + lane;
             const float *bv = F8 ? p.fold8 + size_t(nl + L) * HID : p.bias + size_t(L) * HID;
-            ColConst r{__ldg(bv + col), __ldg(bv + col + 32), 0.f, 0.f};
-            if (F8) {
-                const float *dv = p.fold8 + size_t(L) * HID;
-                r.d0 = __ldg(dv + col);
-                r.d1 = __ldg(dv + col + 32);
-            }
-            return r;
+            return ColConst{__ldg(bv + col), __ldg(bv + col + 32), F8 ? __ldg(p.fold8 + size_t(L) * HID) : 0.f};
         };
         ColConst next_cc = load_cc(0, 0);
         if (g == 0) write_features(blockIdx.x);
@@ -477,13 +472,13 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
                     for (int s = 0; s < 2; ++s) {
                         const int col0 = unit * 64 + s * 32;
                         const uint32_t *a = s == 0 ? a0 : a1;
-                        const float bl = s == 0 ? cc.b0 : cc.b1, dl = s == 0 ? cc.d0 : cc.d1;
+                        const float bl = s == 0 ? cc.b0 : cc.b1;
                         float v[32];
 #pragma unroll
                         for (int j = 0; j < 32; ++j) {
                             const float b = __shfl_sync(0xFFFFFFFFu, bl, j);
                             const float y = __uint_as_float(a[j]);
-                            v[j] = F8 ? fmaf(y, __shfl_sync(0xFFFFFFFFu, dl, j), b) : y + b;
+                            v[j] = F8 ? fmaf(y, cc.d, b) : y + b;
                         }
                         TC_TRACE(trace::kEpiX + (g * trace::kChunks + int(uses)) * 6 + 3 * s + 0, tr);
                         if (fc2) {

@@ -47,16 +47,19 @@ def bf16_weights(p64):
 
 
 def e4m3_weights(p64):
-    """Per-output-channel scale 448 / max|W[:, n]|, E4M3 round-to-nearest-even, dequantised."""
-    def deq(W):
+    """E4M3 round-to-nearest-even of W * 448 / max|W|, dequantised: one scale per hidden layer,
+    one per output column (Wc[:, c]) for the output layer."""
+    def deq(W, per_column=False):
         amax = np.abs(W.astype(np.float32)).max(axis=0)
+        if not per_column:
+            amax = np.full_like(amax, amax.max())
         sw = np.where(amax > 0, np.float32(448.0) / amax.astype(np.float32), np.float32(1.0)).astype(np.float32)
         q = quant.e4m3_round((W.astype(np.float32) * sw[None, :]).astype(np.float32))
         return q / sw[None, :].astype(np.float64)
     q = dict(p64)
     q["W1"] = [deq(w) for w in p64["W1"]]
     q["W2"] = [deq(w) for w in p64["W2"]]
-    q["Wc"] = deq(p64["Wc"])
+    q["Wc"] = deq(p64["Wc"], per_column=True)
     return q
 
 
