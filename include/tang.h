@@ -135,7 +135,7 @@ int tang_rule_conflicts(tang_ctx *ctx, uint32_t rs, uint32_t id, uint32_t *tuple
 /* Precisions of the network's N x N layers. */
 #define TANG_FP32 0 /* FP32 CUDA-core GEMMs */
 #define TANG_BF16 1 /* tcgen05 BF16 MMA, FP32 accumulation */
-#define TANG_FP8 2  /* tcgen05 FP8 E4M3 MMA, FP32 accumulation, per-channel weight scales */
+#define TANG_FP8 2  /* tcgen05 FP8 E4M3 MMA, FP32 accumulation; weight scales per hidden layer and per output column of the output layer, power-of-two activation scales per layer input */
 
 /* Model blob (little-endian), produced by tang_train() or by the caller:
  *   tang_model_header
