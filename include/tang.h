@@ -440,6 +440,20 @@ int tang_du_apply(tang_ctx *ctx, uint32_t rs, int decision, const tang_header *s
  * Synchronous. Errors: TANG_EINVAL (limit out of range), TANG_EDEVICE. */
 int tang_selftest_wait_timeout(tang_ctx *ctx, uint32_t limit_ms, float *elapsed_ms);
 
+/* Checked builds. A library compiled with TANG_CHECKED (paper_2601_03187_b300/build.py
+ * --checked, libtang_checked.so) tests every table index its search code forms (slot, rule
+ * pool, conflict-word row, tuple order) against the table's size before the access. An index
+ * out of range is not accessed; the lookup ends as if it had found nothing, and the next
+ * synchronising call returns TANG_EDEVICE. In other builds the tests are compiled out.
+ * tang_checked_build returns 1 for a checked build, else 0. */
+int tang_checked_build(void);
+
+/* Test hook for the checked build: the ruleset's device descriptor states a rule-pool size of
+ * `n` (0xFFFFFFFF: the real size again), so that rule indices at or past n count as out of
+ * range while the memory they address stays allocated. Classification results are undefined
+ * until the real size is restored. Synchronous. Errors: TANG_ENOTFOUND, TANG_EDEVICE. */
+int tang_debug_set_pool_view(tang_ctx *ctx, uint32_t rs, uint32_t n);
+
 /* ---------------------------------------------------------------------------------------
  * Autotuning and serving
  * ------------------------------------------------------------------------------------- */

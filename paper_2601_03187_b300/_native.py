@@ -133,6 +133,8 @@ _SIGS = {
     "tang_autotune_get": (_I, [_P, _U32, _U32] + [ctypes.POINTER(_I)] * 4 + [ctypes.POINTER(_F)]),
     "tang_selftest_wait_timeout": (_I, [_P, _U32, ctypes.POINTER(_F)]),
     "tang_export_rules": (_I, [_P, _U32, _P, _U32, ctypes.POINTER(_U32)]),
+    "tang_checked_build": (_I, []),
+    "tang_debug_set_pool_view": (_I, [_P, _U32, _U32]),
 }
 
 
@@ -499,6 +501,11 @@ class Context:
         rc = lib.tang_selftest_wait_timeout(self._h, int(limit_ms), ctypes.byref(ms))
         return rc, float(ms.value)
 
+    def debug_set_pool_view(self, rs: int, n=None):
+        """Test hook of checked builds: the ruleset's device descriptor states a rule-pool size of n
+        (None: the real size again); see tang_debug_set_pool_view."""
+        self._ck(lib.tang_debug_set_pool_view(self._h, rs, 0xFFFFFFFF if n is None else int(n)), "debug_set_pool_view")
+
     def serve_start(self, max_inflight=8, max_batch=262144, path="fused_bf16"):
         c = ServeCfg(max_inflight=max_inflight, max_batch=max_batch,
                      path=PATHS[path] if isinstance(path, str) else int(path))
@@ -524,6 +531,11 @@ class Context:
 
 def now() -> float:
     return lib.tang_now()
+
+
+def checked_build() -> bool:
+    """True when the loaded library was built with TANG_CHECKED (tang_checked_build)."""
+    return bool(lib.tang_checked_build())
 
 
 def du_decide(tau: float, theta: int, th_base: float, th_cur: float, suboptimal: int) -> str:

@@ -94,6 +94,9 @@ int tang::check_device_error(tang_ctx *ctx) {
         return set_err(ctx, TANG_EDEVICE, "reading the device error word failed");
     if (bits) {
         cudaMemset(ctx->d_err, 0, sizeof(int));
+        if (bits & kErrIndex)
+            return set_err(ctx, TANG_EDEVICE, "a table index was out of range; the access was skipped (checked build, "
+                                              "error bits 0x%x)", bits);
         return set_err(ctx, TANG_ETIMEOUT, "a device wait ran out of time (error bits 0x%x)", bits);
     }
     return TANG_OK;
@@ -113,6 +116,39 @@ static int variant_of(uint32_t flags) {
 static Ruleset *find_rs(tang_ctx *ctx, uint32_t rs) {
     auto it = ctx->rulesets.find(rs);
     return it == ctx->rulesets.end() ? nullptr : it->second.get();
+}
+
+// Checked builds synchronise after every classify and search call (unless the stream is being
+// captured) and report the device error word, so that an index found out of range surfaces at the
+// call that formed it; other builds check it at the calls that synchronise anyway.
+static int checked_sync(tang_ctx *ctx, cudaStream_t st) {
+#ifdef TANG_CHECKED
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone) {
+        if (cudaStreamSynchronize(st) != cudaSuccess) return set_err(ctx, TANG_EDEVICE, "stream synchronise failed");
+        return check_device_error(ctx);
+    }
+#else
+    (void)ctx;
+    (void)st;
+#endif
+    return TANG_OK;
+}
+
+int tang_checked_build(void) {
+#ifdef TANG_CHECKED
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+int tang_debug_set_pool_view(tang_ctx *ctx, uint32_t rsh, uint32_t n) {
+    if (!ctx) return TANG_EINVAL;
+    Ruleset *rs = find_rs(ctx, rsh);
+    if (!rs) return set_err(ctx, TANG_ENOTFOUND, "unknown ruleset %u", rsh);
+    cudaSetDevice(ctx->device);
+    return tss_set_pool_view(ctx, *rs, n);
 }
 
 extern "C" {
@@ -548,7 +584,7 @@ int tang_classify(tang_ctx *ctx, uint32_t rsh, const tang_header *headers, uint3
         stats->slot_reads = hs.slot_reads;
     }
     if (stats || (flags & TANG_MEM_HOST)) return check_device_error(ctx);
-    return TANG_OK;
+    return checked_sync(ctx, st);
 }
 
 // Host-streamed classification: chunks flow H2D (copy_in stream) -> compute (ctx stream) ->
@@ -685,8 +721,9 @@ int tang_search_ex(tang_ctx *ctx, uint32_t rsh, const tang_header *d_headers, co
         CK(cudaMemcpyAsync(&hs, dst, sizeof(hs), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         std::memcpy(stats, &hs, sizeof(hs));
+        return check_device_error(ctx);
     }
-    return TANG_OK;
+    return checked_sync(ctx, st);
 }
 
 int tang_insert_rule(tang_ctx *ctx, uint32_t rsh, const tang_rule *rule) {

@@ -77,8 +77,15 @@ struct Tables {
     uint32_t T;              // tuples
     uint32_t cw;             // conflict words per rule (ceil(T/32))
     uint32_t pool_size;      // rule pool entries in use (live + dead)
+    uint32_t slot_cap;       // slots allocated (bound of every slot index)
+    uint32_t cword_rows;     // conflict-word rows allocated (T > 32)
     uint32_t pad;
+    int *err;                // the context's device error word (checked builds report into it)
 };
+
+// Device error word bits outside the bounded waits': an index the checked build (TANG_CHECKED)
+// found out of range; the access was skipped.
+constexpr int kErrIndex = 1 << 30;
 
 // Per-call counters (tang_stats in device memory).
 struct DevStats {
@@ -172,6 +179,7 @@ struct Ruleset {
     uint16_t *d_order = nullptr;
     uint32_t slot_capacity = 0, rule_capacity = 0, cword_capacity = 0;  // elements (cwords: words)
     uint32_t cword_rows = 0;  // conflict rows handed out (T > 32 only)
+    uint32_t pool_view = kEmpty;  // test hook: the pool size the device descriptor states (kEmpty: the real one)
     Tables *d_desc = nullptr;
     Tables h_desc{};
     std::unique_ptr<DeviceModel> model;
@@ -236,6 +244,7 @@ int tss_insert(tang_ctx *ctx, Ruleset &rs, const tang_rule &r, cudaStream_t st);
 int tss_delete(tang_ctx *ctx, Ruleset &rs, uint32_t id, cudaStream_t st);
 void tss_free(tang_ctx *ctx, Ruleset &rs);
 int tss_rebuild(tang_ctx *ctx, Ruleset &rs, bool &same_tuples);
+int tss_set_pool_view(tang_ctx *ctx, Ruleset &rs, uint32_t n);
 uint64_t fmix64_host(uint64_t k);
 
 // search.cu

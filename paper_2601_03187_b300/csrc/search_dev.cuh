@@ -6,6 +6,15 @@
 
 namespace tang {
 
+// Checked builds (TANG_CHECKED) test every table index against its table's size before the
+// access; an index out of range sets kErrIndex in the context's error word and the access is
+// skipped (the lookup then ends as if it had found nothing). Other builds compile the test out.
+#ifdef TANG_CHECKED
+#define TANG_INDEX_OK(tb, cond) ((cond) || (atomicOr((tb).err, kErrIndex), false))
+#else
+#define TANG_INDEX_OK(tb, cond) true
+#endif
+
 // MurmurHash3 fmix64 finalizer (Austin Appleby, public domain); same as fmix64_host().
 __device__ __forceinline__ uint64_t fmix64(uint64_t k) {
     k ^= k >> 33;
@@ -70,11 +79,14 @@ __device__ __forceinline__ bool probe_tuple(const Tables &tb, const TupleDesc &d
     const uint32_t ks = h.sip & d.mask_s, kd = h.dip & d.mask_d;
     const uint32_t start = uint32_t(fmix64((uint64_t(ks) << 32) | kd)) & d.slot_mask;
     for (uint32_t i = 0; i <= d.max_probe; ++i) {
-        uint4 s = __ldg(reinterpret_cast<const uint4 *>(tb.slots + d.slot_base + ((start + i) & d.slot_mask)));
+        const uint32_t si = d.slot_base + ((start + i) & d.slot_mask);
+        if (!TANG_INDEX_OK(tb, si < tb.slot_cap)) return false;
+        uint4 s = __ldg(reinterpret_cast<const uint4 *>(tb.slots + si));
         c.slot_reads++;
         if (s.z == kEmpty) return false;
         if (s.x == ks && s.y == kd) {
             for (uint32_t j = 0; j < s.w; ++j) {
+                if (!TANG_INDEX_OK(tb, s.z + j < tb.pool_size)) return false;
                 DRule r = load_rule(tb.rules + s.z + j);
                 c.rule_reads++;
                 if (!beats(r.prio, r.id, best)) return false;
@@ -110,11 +122,14 @@ __device__ __forceinline__ bool search_packet(const Tables &tb, const TupleDesc 
     if (hit) {
         if (tb.cw == 1)
             cf0 = best.cf;
-        else
+        else if (TANG_INDEX_OK(tb, best.cf < tb.cword_rows))
             cfw = tb.cwords + size_t(best.cf) * tb.cw;
+        else
+            return hit;
     }
     for (uint32_t k = 0; k < T; ++k) {
         const uint32_t t = order[k];
+        if (!TANG_INDEX_OK(tb, t < T)) break;
         if (int(t) == pred) continue;
         if (hit) {
             uint32_t w = cfw ? __ldg(cfw + (t >> 5)) : cf0;

@@ -216,9 +216,20 @@ static int upload_desc(tang_ctx *ctx, Ruleset &rs, cudaStream_t st) {
     rs.h_desc.order = rs.d_order;
     rs.h_desc.T = uint32_t(rs.host.tuples.size());
     rs.h_desc.cw = rs.host.cw;
-    rs.h_desc.pool_size = uint32_t(rs.host.pool.size());
+    rs.h_desc.pool_size = rs.pool_view != kEmpty ? rs.pool_view : uint32_t(rs.host.pool.size());
+    rs.h_desc.slot_cap = rs.slot_capacity;
+    rs.h_desc.cword_rows = rs.host.cw > 1 ? rs.cword_capacity / rs.host.cw : 0;
+    rs.h_desc.err = ctx->d_err;
     CKR(cudaMemcpyAsync(rs.d_desc, &rs.h_desc, sizeof(Tables), cudaMemcpyHostToDevice, st));
     return TANG_OK;
+}
+
+// Test hook: make the device descriptor state a pool size of n (kEmpty: the real size again).
+int tss_set_pool_view(tang_ctx *ctx, Ruleset &rs, uint32_t n) {
+    rs.pool_view = n;
+    int rc = upload_desc(ctx, rs, ctx->stream);
+    if (!rc) CKR(cudaStreamSynchronize(ctx->stream));
+    return rc;
 }
 
 int tss_upload(tang_ctx *ctx, Ruleset &rs, cudaStream_t st) {
