@@ -48,7 +48,7 @@ def flops_per_packet(T):
 # reported only while the kernel's sources and the packet count are the ones it was taken with.
 TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "k_tc256_classify_bf16_dram_512k_16M.md")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_2601_03187_b300", "csrc", f)
-                  for f in ("mlp_tc256.cu", "search_dev.cuh", "tc_ptx.cuh", "tc_common.cuh")]
+                  for f in ("mlp_tc256.cu", "search_dev.cuh", "tc_ptx.cuh", "tc_common.cuh", "internal.h")]
 
 
 def kernel_digest():

@@ -224,6 +224,7 @@ int tang_memory_usage(tang_ctx *ctx, size_t *used, size_t *cap) {
 }
 
 int tang_load_ruleset(tang_ctx *ctx, const tang_rule *rules, uint32_t n, uint32_t *rs_out) {
+    const NvtxRange nvtx_range("tang_load_ruleset");
     if (!ctx || !rs_out || (n && !rules)) return set_err(ctx, TANG_EINVAL, "null argument");
     cudaSetDevice(ctx->device);
     auto t0 = std::chrono::steady_clock::now();
@@ -364,6 +365,7 @@ static bool swap_in_place(tang_ctx *ctx, DeviceModel &live, const DeviceModel &n
 }
 
 int tang_load_model(tang_ctx *ctx, uint32_t rsh, const void *blob, size_t bytes) {
+    const NvtxRange nvtx_range("tang_load_model");
     if (!ctx || !blob) return set_err(ctx, TANG_EINVAL, "null argument");
     Ruleset *rs = find_rs(ctx, rsh);
     if (!rs) return set_err(ctx, TANG_ENOTFOUND, "unknown ruleset %u", rsh);
@@ -516,6 +518,7 @@ static int classify_host(tang_ctx *ctx, Ruleset &rs, const tang_header *h, uint3
 
 int tang_classify(tang_ctx *ctx, uint32_t rsh, const tang_header *headers, uint32_t n, uint32_t *ids, uint32_t flags,
                   void *stream, tang_stats *stats) {
+    const NvtxRange nvtx_range("tang_classify");
     if (!ctx) return TANG_EINVAL;
     Ruleset *rs = find_rs(ctx, rsh);
     if (!rs) return set_err(ctx, TANG_ENOTFOUND, "unknown ruleset %u", rsh);
@@ -685,6 +688,7 @@ static int classify_host(tang_ctx *ctx, Ruleset &rs, const tang_header *h, uint3
 
 int tang_infer(tang_ctx *ctx, uint32_t rsh, const tang_header *d_headers, uint32_t n, float *d_logits,
                int32_t *d_tuple, int precision, void *stream) {
+    const NvtxRange nvtx_range("tang_infer");
     if (!ctx) return TANG_EINVAL;
     Ruleset *rs = find_rs(ctx, rsh);
     if (!rs) return set_err(ctx, TANG_ENOTFOUND, "unknown ruleset %u", rsh);
@@ -703,6 +707,7 @@ int tang_search(tang_ctx *ctx, uint32_t rsh, const tang_header *d_headers, const
 
 int tang_search_ex(tang_ctx *ctx, uint32_t rsh, const tang_header *d_headers, const int32_t *d_tuple, uint32_t n,
                    uint32_t *d_ids, uint32_t flags, void *stream, tang_stats *stats) {
+    const NvtxRange nvtx_range("tang_search_ex");
     if (!ctx) return TANG_EINVAL;
     Ruleset *rs = find_rs(ctx, rsh);
     if (!rs) return set_err(ctx, TANG_ENOTFOUND, "unknown ruleset %u", rsh);
@@ -727,6 +732,7 @@ int tang_search_ex(tang_ctx *ctx, uint32_t rsh, const tang_header *d_headers, co
 }
 
 int tang_insert_rule(tang_ctx *ctx, uint32_t rsh, const tang_rule *rule) {
+    const NvtxRange nvtx_range("tang_insert_rule");
     if (!ctx || !rule) return set_err(ctx, TANG_EINVAL, "null argument");
     Ruleset *rs = find_rs(ctx, rsh);
     if (!rs) return set_err(ctx, TANG_ENOTFOUND, "unknown ruleset %u", rsh);
@@ -739,6 +745,7 @@ int tang_insert_rule(tang_ctx *ctx, uint32_t rsh, const tang_rule *rule) {
 }
 
 int tang_delete_rule(tang_ctx *ctx, uint32_t rsh, uint32_t id) {
+    const NvtxRange nvtx_range("tang_delete_rule");
     if (!ctx) return TANG_EINVAL;
     Ruleset *rs = find_rs(ctx, rsh);
     if (!rs) return set_err(ctx, TANG_ENOTFOUND, "unknown ruleset %u", rsh);

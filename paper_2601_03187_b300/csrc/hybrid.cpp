@@ -234,6 +234,7 @@ class SearchPool {
 
 extern "C" int tang_classify_hybrid(tang_ctx *ctx, uint32_t rsh, const tang_header *headers, uint32_t n, uint32_t *ids,
                                     const tang_hybrid_cfg *cfg, tang_stats *stats) {
+    const NvtxRange nvtx_range("tang_classify_hybrid");
     if (!ctx || !cfg) return set_err(ctx, TANG_EINVAL, "null argument");
     auto it = ctx->rulesets.find(rsh);
     if (it == ctx->rulesets.end()) return set_err(ctx, TANG_ENOTFOUND, "unknown ruleset %u", rsh);

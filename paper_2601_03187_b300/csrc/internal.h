@@ -15,9 +15,20 @@
 #include <unordered_map>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "tang.h"
 
 namespace tang {
+
+// A named NVTX range around one library call, for profilers' timelines (nearly free when no
+// tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 constexpr uint32_t kEmpty = 0xFFFFFFFFu;
 constexpr uint32_t kMaxTuples = 2047;  // tuple index is stored in 11 bits of a rule record

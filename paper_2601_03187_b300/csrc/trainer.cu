@@ -535,6 +535,7 @@ int train_run(tang_ctx *ctx, Ruleset &rs, const tang_header *samples, uint32_t n
 
 extern "C" int tang_train(tang_ctx *ctx, uint32_t rsh, const tang_header *samples, uint32_t n,
                           const tang_train_cfg *cfg, void *blob, size_t *bytes, tang_train_report *report) {
+    const NvtxRange nvtx_range("tang_train");
     if (!ctx || !samples || !cfg || !bytes || n == 0) return set_err(ctx, TANG_EINVAL, "bad argument");
     auto it = ctx->rulesets.find(rsh);
     if (it == ctx->rulesets.end()) return set_err(ctx, TANG_ENOTFOUND, "unknown ruleset %u", rsh);

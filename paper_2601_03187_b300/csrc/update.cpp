@@ -68,6 +68,7 @@ int tang_du_close_window(tang_ctx *ctx, uint32_t rsh, const tang_du_cfg *cfg, ta
 
 int tang_finetune(tang_ctx *ctx, uint32_t rsh, const tang_header *samples, uint32_t n, const tang_train_cfg *cfg,
                   void *blob, size_t *bytes, tang_train_report *report) {
+    const NvtxRange nvtx_range("tang_finetune");
     if (!ctx || !samples || !cfg || !bytes || n == 0) return set_err(ctx, TANG_EINVAL, "bad argument");
     Ruleset *rs = du_find(ctx, rsh);
     if (!rs) return set_err(ctx, TANG_ENOTFOUND, "unknown ruleset %u", rsh);
@@ -83,6 +84,7 @@ int tang_finetune(tang_ctx *ctx, uint32_t rsh, const tang_header *samples, uint3
 }
 
 int tang_rebuild_ruleset(tang_ctx *ctx, uint32_t rsh, int *model_kept) {
+    const NvtxRange nvtx_range("tang_rebuild_ruleset");
     if (!ctx) return TANG_EINVAL;
     Ruleset *rs = du_find(ctx, rsh);
     if (!rs) return set_err(ctx, TANG_ENOTFOUND, "unknown ruleset %u", rsh);
@@ -107,6 +109,7 @@ int tang_rebuild_ruleset(tang_ctx *ctx, uint32_t rsh, int *model_kept) {
 
 int tang_du_apply(tang_ctx *ctx, uint32_t rsh, int decision, const tang_header *samples, uint32_t n,
                   const tang_train_cfg *cfg, tang_train_report *report) {
+    const NvtxRange nvtx_range("tang_du_apply");
     if (!ctx) return TANG_EINVAL;
     Ruleset *rs = du_find(ctx, rsh);
     if (!rs) return set_err(ctx, TANG_ENOTFOUND, "unknown ruleset %u", rsh);
