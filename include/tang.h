@@ -472,6 +472,15 @@ int tang_autotune(tang_ctx *ctx, uint32_t rs, const tang_header *d_headers, uint
 int tang_autotune_get(tang_ctx *ctx, uint32_t rs, uint32_t path, int *variant, int *grid, int *search_threads,
                       int *search_bps, float *ms);
 
+/* Set the launch shape of (rs, path) as tang_autotune would, e.g. one saved from
+ * tang_autotune_get in an earlier process, so that a restart needs no new tuning. Values as in
+ * tang_autotune_get (0 = default for each): variant 0-5 (1-4 only for N == 512, 6 blocks,
+ * C <= 128), grid 0 to the SM count, search_threads 0 / 128 / 256 / 512, search_bps 0-16 with
+ * threads x blocks <= 2048. Drops captured graphs. Errors: TANG_ENOTFOUND, TANG_EINVAL (a value
+ * out of range, or variant 1-4 for a model they cannot run). */
+int tang_autotune_set(tang_ctx *ctx, uint32_t rs, uint32_t path, int variant, int grid, int search_threads,
+                      int search_bps);
+
 typedef struct tang_serve_cfg {
     uint32_t max_inflight;   /* requests on the GPU at once (slots) */
     uint32_t max_batch;      /* packets per GPU launch (requests are packed up to this) */

@@ -134,6 +134,7 @@ _SIGS = {
     "tang_selftest_wait_timeout": (_I, [_P, _U32, ctypes.POINTER(_F)]),
     "tang_export_rules": (_I, [_P, _U32, _P, _U32, ctypes.POINTER(_U32)]),
     "tang_checked_build": (_I, []),
+    "tang_autotune_set": (_I, [_P, _U32, _U32, _I, _I, _I, _I]),
     "tang_debug_set_pool_view": (_I, [_P, _U32, _U32]),
 }
 
@@ -494,6 +495,13 @@ class Context:
         names = {0: "default", 1: "1sm", 2: "2sm", 3: "mc2", 4: "mc4", 5: "n256"}
         return {"variant": names.get(v[0].value, str(v[0].value)), "grid": v[1].value, "search_threads": v[2].value,
                 "search_bps": v[3].value, "ms": round(ms.value, 4)}
+
+    def autotune_set(self, rs: int, path="fused_bf16", variant="default", grid=0, search_threads=0, search_bps=0):
+        """Set (rs, path)'s launch shape, e.g. a dict saved from autotune_get (tang_autotune_set)."""
+        names = {"default": 0, "1sm": 1, "2sm": 2, "mc2": 3, "mc4": 4, "n256": 5}
+        v = names[variant] if isinstance(variant, str) else int(variant)
+        self._ck(lib.tang_autotune_set(self._h, rs, PATHS[path] if isinstance(path, str) else int(path), v, int(grid),
+                                       int(search_threads), int(search_bps)), "autotune_set")
 
     def selftest_wait_timeout(self, limit_ms: int = 50):
         """(return code, kernel ms) of tang_selftest_wait_timeout; TANG_ETIMEOUT is the designed outcome."""

@@ -100,6 +100,32 @@ extern "C" int tang_autotune(tang_ctx *ctx, uint32_t rsh, const tang_header *d_h
     return TANG_OK;
 }
 
+extern "C" int tang_autotune_set(tang_ctx *ctx, uint32_t rsh, uint32_t path, int variant, int grid, int search_threads,
+                                 int search_bps) {
+    if (!ctx) return TANG_EINVAL;
+    auto it = ctx->rulesets.find(rsh);
+    if (it == ctx->rulesets.end()) return set_err(ctx, TANG_ENOTFOUND, "unknown ruleset %u", rsh);
+    const Ruleset &rs = *it->second;
+    if (variant < 0 || variant > 5 || grid < 0 || grid > ctx->sm_count)
+        return set_err(ctx, TANG_EINVAL, "variant %d / grid %d out of range", variant, grid);
+    if (variant >= 1 && variant <= 4 &&
+        !(rs.model && rs.model->N == 512 && rs.model->layers == 12 && rs.model->C <= 128))
+        return set_err(ctx, TANG_EINVAL, "variant %d needs a loaded 6-block, width-512 model of at most 128 classes",
+                       variant);
+    const bool th_ok = search_threads == 0 || search_threads == 128 || search_threads == 256 || search_threads == 512;
+    if (!th_ok || search_bps < 0 || search_bps > 16 || search_threads * search_bps > 2048)
+        return set_err(ctx, TANG_EINVAL, "search launch %d threads x %d blocks per SM out of range", search_threads,
+                       search_bps);
+    TuneEntry e;
+    e.fused_variant = variant;
+    e.fused_grid = grid;
+    e.search_threads = search_threads;
+    e.search_bps = search_bps;
+    it->second->tune[path & TANG_PATH_MASK] = e;
+    drop_graphs_of(ctx);  // graphs captured the previous launch shape
+    return TANG_OK;
+}
+
 extern "C" int tang_autotune_get(tang_ctx *ctx, uint32_t rsh, uint32_t path, int *variant, int *grid, int *search_threads,
                                  int *search_bps, float *ms) {
     if (!ctx) return TANG_EINVAL;

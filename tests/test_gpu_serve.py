@@ -105,3 +105,34 @@ def test_autotune_keeps_ids_exact():
             ctx.classify(rs, d, ids, path=path, graph=True)
             torch.cuda.synchronize()
             assert (ids_host(ids) == want).all(), path
+
+
+def test_tuned_shapes_restore_in_a_new_context():
+    """A launch shape saved from autotune_get and set in a fresh context (a restart) is the one
+    the new context reports and runs, with exact ids; values out of range are refused."""
+    saved = {}
+    with tg.Context(0) as ctx:
+        (rs, rules), = load_rulesets(ctx, [20000])
+        h = wl.gen_trace(rules, [("inside", 100000)], 9)
+        d = to_dev(h)
+        for path in ("no_nn", "fused_bf16"):
+            ctx.autotune(rs, d, path=path)
+            saved[path] = ctx.autotune_get(rs, path)
+    with tg.Context(0) as ctx:
+        (rs, rules2), = load_rulesets(ctx, [20000])
+        assert (rules2 == rules).all()
+        d = to_dev(h)
+        want = oc.classify(rules, h)
+        for path, c in saved.items():
+            ctx.autotune_set(rs, path, variant=c["variant"], grid=c["grid"], search_threads=c["search_threads"],
+                             search_bps=c["search_bps"])
+            got = ctx.autotune_get(rs, path)
+            assert {k: got[k] for k in ("variant", "grid", "search_threads", "search_bps")} == \
+                   {k: c[k] for k in ("variant", "grid", "search_threads", "search_bps")}
+            ids = ids_dev(len(h))
+            ctx.classify(rs, d, ids, path=path, graph=True)
+            torch.cuda.synchronize()
+            assert (ids_host(ids) == want).all(), path
+        for bad in ({"variant": 6}, {"grid": 100000}, {"search_threads": 96}, {"search_threads": 512, "search_bps": 8}):
+            with pytest.raises(tg.TangError):
+                ctx.autotune_set(rs, "no_nn", **bad)
