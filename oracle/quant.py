@@ -30,6 +30,15 @@ def bf16_round(x) -> np.ndarray:
     return bf16_value(bf16_bits(x))
 
 
+def bf16_round64(x) -> np.ndarray:
+    """float64 values rounded once, to nearest with ties to even, to the nearest BF16 value (8
+    significant bits), returned as float64. Rounding a float64 to float32 first and then to BF16
+    can differ (double rounding); this does not. Inputs stay inside BF16's normal range here."""
+    x = np.asarray(x, dtype=np.float64)
+    m, e = np.frexp(x)                     # x = m * 2^e, 0.5 <= |m| < 1
+    return np.ldexp(np.rint(m * 256.0) / 256.0, e)   # np.rint rounds halves to even
+
+
 E4M3_MAX = 448.0
 
 
