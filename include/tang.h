@@ -157,9 +157,7 @@ typedef struct tang_model_header {
 /* Validate and upload a model for ruleset `rs`; keeps an FP32 copy and derives the BF16 and
  * (if calibrated) FP8 copies. Requires C == n_tuples, S == 7. The tensor-core paths further
  * require N == 256 or 512 and 1 <= blocks <= 31 (other shapes use the FP32 path only); the
- * default N=256 kernel takes any C (its output layer runs in 256-column chunks), the N=128
- * variants (TANG_FUSED_1SM, _2SM, _MCAST2/4) serve only N == 512, blocks == 6 and C <= 128, and
- * other models always run the N=256 kernel.
+ * fused kernel takes any C (its output layer runs in 256-column chunks).
  * Replaces a previous model of the ruleset. Synchronous: waits for all work on the device.
  * Hot swap (§5.2.2 deploys retrained weights while classification goes on): when the previous
  * model has the same S, N, blocks, C and FP8 calibration state, the new weights are written into
@@ -189,19 +187,19 @@ int tang_load_model(tang_ctx *ctx, uint32_t rs, const void *blob, size_t bytes);
 #define TANG_GRAPH 0x100          /* DEVICE mode: capture the launch sequence in a CUDA graph
                                      keyed by (ruleset, path, n, pointers, stream) and replay it */
 /* Tensor-core kernel variant (fused and staged paths, and tang_infer's precision argument);
- * neither bit = the autotuned choice, else the library default. */
-#define TANG_FUSED_1SM 0x200      /* one CTA per SM, M = 128 packets, 128-wide MMAs, 2 accumulators */
-#define TANG_FUSED_2SM 0x400      /* CTA pairs (cta_group::2), M = 256 packets per MMA */
-#define TANG_FUSED_MCAST2 0x800   /* 1-SM MMAs; clusters of 2 CTAs share each weight tile (TMA multicast) */
-#define TANG_FUSED_MCAST4 0x1000  /* same with clusters of 4 CTAs */
+ * no bit = the autotuned choice, else the library default. */
 #define TANG_FUSED_N256 0x2000    /* one CTA per SM, 256-wide MMAs, single-buffered accumulator */
-#define TANG_VARIANT_MASK 0x3E00
+#define TANG_VARIANT_MASK 0x2000
 /* Post-verification exactly as §5.1.1 prints it, for measurement only: a match in the predicted
  * tuple is returned at once, without the conflict-set probes, so a packet can get a
  * lower-priority rule when the network predicts a wrong tuple that also holds a match (the case
  * §5.1.1 and §8 leave uncorrected); a miss still searches the other tuples in order. Combines
  * with every path; the default (flag clear) is the exact search. */
 #define TANG_SEARCH_PAPER 0x4000
+/* Scan every rule run with one thread, as the first builds did, instead of letting the lanes of a
+ * warp scan a long run (more than 16 rules under one key) together with coalesced reads; for
+ * measurement. Ids and counters are the same either way. Combines with every path. */
+#define TANG_SEARCH_SERIAL 0x8000
 
 typedef struct tang_stats {
     uint64_t packets;       /* packets classified */
@@ -226,8 +224,8 @@ int tang_classify(tang_ctx *ctx, uint32_t rs, const tang_header *headers, uint32
 /* Stage 1 alone (§5.1.1): run the network of ruleset rs over n device headers.
  * d_logits (device, n x C float, row-major; may be NULL) receives the output layer's logits;
  * d_tuple (device, n int32; may be NULL) the argmax (lowest index on ties).
- * precision: TANG_FP32 / TANG_BF16 / TANG_FP8, optionally OR-ed with TANG_FUSED_1SM or
- * TANG_FUSED_2SM to pick the tensor-core kernel variant. Asynchronous on `stream`. */
+ * precision: TANG_FP32 / TANG_BF16 / TANG_FP8, optionally OR-ed with a TANG_FUSED_* variant bit.
+ * Asynchronous on `stream`. */
 int tang_infer(tang_ctx *ctx, uint32_t rs, const tang_header *d_headers, uint32_t n, float *d_logits,
                int32_t *d_tuple, int precision, void *stream);
 
@@ -237,7 +235,8 @@ int tang_infer(tang_ctx *ctx, uint32_t rs, const tang_header *d_headers, uint32_
 int tang_search(tang_ctx *ctx, uint32_t rs, const tang_header *d_headers, const int32_t *d_tuple, uint32_t n,
                 uint32_t *d_ids, void *stream, tang_stats *stats);
 
-/* tang_search with flags: 0 (exact search, same as tang_search) or TANG_SEARCH_PAPER.
+/* tang_search with flags: 0 (exact search, same as tang_search), TANG_SEARCH_PAPER and / or
+ * TANG_SEARCH_SERIAL.
  * Errors as tang_search, plus TANG_EINVAL for unknown flag bits. */
 int tang_search_ex(tang_ctx *ctx, uint32_t rs, const tang_header *d_headers, const int32_t *d_tuple, uint32_t n,
                    uint32_t *d_ids, uint32_t flags, void *stream, tang_stats *stats);
@@ -275,25 +274,29 @@ int tang_classify_hybrid(tang_ctx *ctx, uint32_t rs, const tang_header *headers,
  * latency-bound loops that cannot take the device synchronisation cudaMalloc implies.
  * tang_classify may grow the context's scratch buffer with cudaMalloc; this entry point instead
  * passes the predicted tuples between the two kernels through a static device array of
- * TANG_NOALLOC_MAX_PACKETS int32 entries (4 MiB) that every GPU loading the library holds until
- * the process exits. It calls no cudaMalloc, cudaFree or allocating library routine.
+ * TANG_NOALLOC_MAX_PACKETS int32 entries (4 MiB). The array belongs to the library's device
+ * module: a GPU holds it from the moment that module is loaded there (at the latest when a
+ * context is created on it) until the process exits. tang_create looks up the array's device
+ * address, so this call loads no module and calls no cudaMalloc, cudaFree or allocating library
+ * routine.
  * The paper has no counterpart; it is an addition of this library.
  *   d_headers: n device headers, 16-byte aligned; d_ids: n device outputs (same ids as
  *   tang_classify). Requires a loaded model with a tensor-core copy (see tang_load_model).
- *   The first call on a device looks up the array's device address (cudaGetSymbolAddress),
- *   so make that first call before any stream capture that should contain later calls.
  *   All calls share the one array: calls whose kernels overlap on the GPU (on different
  *   streams, or from different contexts on the same device) race and must be serialised.
  *   Asynchronous on `stream` (NULL = the context's stream).
  * Errors: TANG_EINVAL (n > TANG_NOALLOC_MAX_PACKETS, unaligned or null buffers, no model),
- * TANG_ENOTFOUND, TANG_EDEVICE. */
+ * TANG_EUNSUPPORTED (the model has no tensor-core copy), TANG_ENOTFOUND, TANG_EDEVICE. */
 #define TANG_NOALLOC_MAX_PACKETS 1048576u
 int tang_classify_noalloc(tang_ctx *ctx, uint32_t rs, const tang_header *d_headers, uint32_t n, uint32_t *d_ids,
                           void *stream);
 
 /* ---------------------------------------------------------------------------------------
  * Immediate update (§5.2.1). Stream-ordered: every classify issued after the call (on any
- * stream) sees it. Neither call creates or removes a tuple, so a loaded model stays valid.
+ * stream) sees it, and it waits for every classification already issued against the ruleset
+ * (on any stream) before it rewrites the tables, so those see the ruleset as it was. Work
+ * captured into a CUDA graph by the caller is ordered by the caller. Neither call creates or
+ * removes a tuple, so a loaded model stays valid.
  * ------------------------------------------------------------------------------------- */
 
 /* Insert into the tuple with the rule's exact lengths, else into the first tuple of largest
@@ -459,13 +462,13 @@ int tang_debug_set_pool_view(tang_ctx *ctx, uint32_t rs, uint32_t n);
  * ------------------------------------------------------------------------------------- */
 
 /* Time the launch variants of a path on `n` device headers and keep the fastest per
- * (ruleset, path): for the fused paths the tensor-core kernel variant and its persistent CTA
- * count, for the search-kernel paths the block size and blocks per SM. Drops captured graphs
+ * (ruleset, path): for the fused paths the persistent CTA count of the tensor-core kernel, for
+ * the search-kernel paths the block size and blocks per SM. Drops captured graphs
  * (they hold the previous launch shape). Synchronous. */
 int tang_autotune(tang_ctx *ctx, uint32_t rs, const tang_header *d_headers, uint32_t n, uint32_t flags);
 
 /* The launch shape tang_autotune chose for (rs, path): variant = the fused kernel variant
- * (0 = library default, 1 = N=128 one SM, 2 = CTA pairs, 3 / 4 = clusters of 2 / 4, 5 = N=256),
+ * (0 = library default, 5 = the N=256 kernel),
  * grid = persistent CTAs (0 = one per SM), search_threads / search_bps = the search kernel's
  * block size and blocks per SM (0 = default), ms = the time per call measured for the choice
  * (0 if the path was never tuned). Outputs may be NULL. */
@@ -474,10 +477,9 @@ int tang_autotune_get(tang_ctx *ctx, uint32_t rs, uint32_t path, int *variant, i
 
 /* Set the launch shape of (rs, path) as tang_autotune would, e.g. one saved from
  * tang_autotune_get in an earlier process, so that a restart needs no new tuning. Values as in
- * tang_autotune_get (0 = default for each): variant 0-5 (1-4 only for N == 512, 6 blocks,
- * C <= 128), grid 0 to the SM count, search_threads 0 / 128 / 256 / 512, search_bps 0-16 with
- * threads x blocks <= 2048. Drops captured graphs. Errors: TANG_ENOTFOUND, TANG_EINVAL (a value
- * out of range, or variant 1-4 for a model they cannot run). */
+ * tang_autotune_get (0 = default for each): variant 0 or 5, grid 0 to the SM count,
+ * search_threads 0 / 128 / 256 / 512, search_bps 0-16 with threads x blocks <= 2048. Drops
+ * captured graphs. Errors: TANG_ENOTFOUND, TANG_EINVAL (a value out of range). */
 int tang_autotune_set(tang_ctx *ctx, uint32_t rs, uint32_t path, int variant, int grid, int search_threads,
                       int search_bps);
 
@@ -493,8 +495,17 @@ typedef struct tang_req_stats {
 } tang_req_stats;
 
 /* Start the continuous-batching engine: a host thread packs queued requests (of any
- * rulesets) into GPU launches as slots and pool memory free up, overlaps their work on
- * several streams, and completes requests out of order. */
+ * rulesets) into GPU launches as slots and memory free up, overlaps their work on several
+ * streams, and completes requests out of order. Memory admission: a slot's device buffers
+ * ((16 + 4) * max_batch bytes) are taken from the context's pool (from the device's free memory
+ * when the pool is unbounded) only when queued work finds every admitted slot busy, and given
+ * back after the slot has been idle for 20 ms; a refused admission waits for a slot to finish.
+ * So the slots in flight follow the free memory: rulesets or models loaded while the engine runs
+ * lower them, unloads raise them. When no slot can be admitted with nothing in flight for 1 s,
+ * the queued requests complete with TANG_ENOMEM. Pinned staging, streams and events for
+ * max_inflight slots are created here.
+ * Errors: TANG_EINVAL (engine running, path other than fused or no-network, max_inflight not in
+ * 1..64, max_batch 0), TANG_ENOMEM (one slot exceeds the pool or the device). */
 int tang_serve_start(tang_ctx *ctx, const tang_serve_cfg *cfg);
 /* Queue a request of n host headers against ruleset rs; ids (host, n entries) is written
  * before the request completes. Both buffers must stay valid until then. */
@@ -503,6 +514,19 @@ int tang_serve_submit(tang_ctx *ctx, uint32_t rs, const tang_header *headers, ui
 /* TANG_OK when done (stats filled, may be NULL), TANG_EAGAIN while pending after waiting up
  * to wait_ms, TANG_ENOTFOUND for an unknown id. A completed id is forgotten after poll. */
 int tang_serve_poll(tang_ctx *ctx, uint64_t req_id, int wait_ms, tang_req_stats *stats);
+typedef struct tang_serve_info {
+    uint32_t slots_max;           /* max_inflight */
+    uint32_t slots_admitted;      /* slots holding device buffers now */
+    uint32_t slots_admitted_peak; /* most slots held at once since the engine started */
+    uint32_t slots_busy;          /* slots with a launch in flight */
+    uint64_t admissions_refused;  /* slot admissions refused for lack of memory */
+    uint64_t launches, packets;   /* GPU launches issued and packets in them */
+    uint64_t slot_bytes;          /* device bytes one admitted slot holds */
+    uint32_t queued;              /* requests waiting for a slot */
+    uint32_t reserved;
+} tang_serve_info;
+/* Counters of the running engine. Errors: TANG_EINVAL (no engine). */
+int tang_serve_info_get(tang_ctx *ctx, tang_serve_info *out);
 /* Drain and stop. */
 int tang_serve_stop(tang_ctx *ctx);
 /* Seconds on the clock used by tang_req_stats. */

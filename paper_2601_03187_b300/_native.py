@@ -27,9 +27,10 @@ PATHS = {
     "staged_bf16": PATH_STAGED_BF16, "no_nn": PATH_NO_NN, "staged_fp8": PATH_STAGED_FP8,
 }
 MEM_DEVICE, MEM_HOST, GRAPH = 0x00, 0x10, 0x100
-FUSED_1SM, FUSED_2SM, FUSED_MCAST2, FUSED_MCAST4, FUSED_N256 = 0x200, 0x400, 0x800, 0x1000, 0x2000
-VARIANTS = {None: 0, "1sm": FUSED_1SM, "2sm": FUSED_2SM, "mc2": FUSED_MCAST2, "mc4": FUSED_MCAST4, "n256": FUSED_N256}
+FUSED_N256 = 0x2000
+VARIANTS = {None: 0, "n256": FUSED_N256}
 SEARCH_PAPER = 0x4000
+SEARCH_SERIAL = 0x8000
 DU_NONE, DU_INCREMENTAL, DU_RETRAIN = 0, 1, 2
 DU_DECISIONS = {DU_NONE: "none", DU_INCREMENTAL: "incremental", DU_RETRAIN: "retrain"}
 MODEL_MAGIC = 0x474E4154
@@ -89,6 +90,13 @@ class ServeCfg(ctypes.Structure):
                 ("reserved", ctypes.c_uint32)]
 
 
+class ServeInfo(ctypes.Structure):
+    _fields_ = [("slots_max", ctypes.c_uint32), ("slots_admitted", ctypes.c_uint32),
+                ("slots_admitted_peak", ctypes.c_uint32), ("slots_busy", ctypes.c_uint32),
+                ("admissions_refused", ctypes.c_uint64), ("launches", ctypes.c_uint64), ("packets", ctypes.c_uint64),
+                ("slot_bytes", ctypes.c_uint64), ("queued", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
 class ReqStats(ctypes.Structure):
     _fields_ = [("submit_s", ctypes.c_double), ("start_s", ctypes.c_double), ("done_s", ctypes.c_double)]
 
@@ -119,6 +127,7 @@ _SIGS = {
     "tang_serve_submit": (_I, [_P, _U32, _P, _U32, _P, ctypes.POINTER(_U64)]),
     "tang_serve_poll": (_I, [_P, _U64, _I, ctypes.POINTER(ReqStats)]),
     "tang_serve_stop": (_I, [_P]),
+    "tang_serve_info_get": (_I, [_P, ctypes.POINTER(ServeInfo)]),
     "tang_now": (ctypes.c_double, []),
     "tang_classify_noalloc": (_I, [_P, _U32, _P, _U32, _P, _P]),
     "tang_search_ex": (_I, [_P, _U32, _P, _P, _U32, _P, _U32, _P, ctypes.POINTER(Stats)]),
@@ -321,10 +330,11 @@ class Context:
 
     # -- classification ---------------------------------------------------------------------
     def classify(self, rs: int, headers, ids, path="fused_bf16", graph=False, stream=None, stats=False, variant=None,
-                 paper=False):
+                 paper=False, serial=False):
         """ids[i] = matching rule id. numpy headers/ids -> host mode; torch CUDA tensors -> device mode.
-        variant: None (tuned / default), "1sm" or "2sm" tensor-core kernel. paper: the paper's
-        non-exact post-verification (TANG_SEARCH_PAPER), for measurement."""
+        variant: None (tuned / default) or "n256" tensor-core kernel. paper: the paper's
+        non-exact post-verification (TANG_SEARCH_PAPER), for measurement. serial: one thread per
+        rule run (TANG_SEARCH_SERIAL), for measurement."""
         host = isinstance(headers, np.ndarray)
         flags = (PATHS[path] if isinstance(path, str) else int(path)) | VARIANTS[variant]
         flags |= MEM_HOST if host else MEM_DEVICE
@@ -332,6 +342,8 @@ class Context:
             flags |= GRAPH
         if paper:
             flags |= SEARCH_PAPER
+        if serial:
+            flags |= SEARCH_SERIAL
         n = _n_headers(headers)
         st = Stats()
         self._ck(lib.tang_classify(self._h, rs, _ptr(headers), n, _ptr(ids), flags,
@@ -344,11 +356,11 @@ class Context:
         self._ck(lib.tang_infer(self._h, rs, _ptr(headers), n, _ptr(logits), _ptr(tuples),
                                 precision | VARIANTS[variant], _stream(stream)), "infer")
 
-    def search(self, rs: int, headers, tuples, ids, stream=None, stats=False, paper=False):
+    def search(self, rs: int, headers, tuples, ids, stream=None, stats=False, paper=False, serial=False):
         n = _n_headers(headers)
         st = Stats()
         self._ck(lib.tang_search_ex(self._h, rs, _ptr(headers), _ptr(tuples), n, _ptr(ids),
-                                    SEARCH_PAPER if paper else 0, _stream(stream),
+                                    (SEARCH_PAPER if paper else 0) | (SEARCH_SERIAL if serial else 0), _stream(stream),
                                     ctypes.byref(st) if stats else None), "search")
         return st.as_dict() if stats else None
 
@@ -492,13 +504,13 @@ class Context:
         ms = ctypes.c_float()
         self._ck(lib.tang_autotune_get(self._h, rs, PATHS[path] if isinstance(path, str) else int(path),
                                        *[ctypes.byref(x) for x in v], ctypes.byref(ms)), "autotune_get")
-        names = {0: "default", 1: "1sm", 2: "2sm", 3: "mc2", 4: "mc4", 5: "n256"}
+        names = {0: "default", 5: "n256"}
         return {"variant": names.get(v[0].value, str(v[0].value)), "grid": v[1].value, "search_threads": v[2].value,
                 "search_bps": v[3].value, "ms": round(ms.value, 4)}
 
     def autotune_set(self, rs: int, path="fused_bf16", variant="default", grid=0, search_threads=0, search_bps=0):
         """Set (rs, path)'s launch shape, e.g. a dict saved from autotune_get (tang_autotune_set)."""
-        names = {"default": 0, "1sm": 1, "2sm": 2, "mc2": 3, "mc4": 4, "n256": 5}
+        names = {"default": 0, "n256": 5}
         v = names[variant] if isinstance(variant, str) else int(variant)
         self._ck(lib.tang_autotune_set(self._h, rs, PATHS[path] if isinstance(path, str) else int(path), v, int(grid),
                                        int(search_threads), int(search_bps)), "autotune_set")
@@ -532,6 +544,12 @@ class Context:
             return None
         self._ck(rc, "serve_poll")
         return {"submit_s": st.submit_s, "start_s": st.start_s, "done_s": st.done_s}
+
+    def serve_info(self) -> dict:
+        """Counters of the running serving engine (tang_serve_info_get)."""
+        i = ServeInfo()
+        self._ck(lib.tang_serve_info_get(self._h, ctypes.byref(i)), "serve_info")
+        return {k: getattr(i, k) for k, _ in ServeInfo._fields_ if k != "reserved"}
 
     def serve_stop(self):
         self._ck(lib.tang_serve_stop(self._h), "serve_stop")

@@ -18,7 +18,7 @@ BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libtang.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
-SOURCES = ["api.cu", "tss_host.cpp", "search.cu", "mlp_simt.cu", "trainer.cu", "mlp_tc.cu", "mlp_tc2.cu", "mlp_tc256.cu",
+SOURCES = ["api.cu", "tss_host.cpp", "search.cu", "mlp_simt.cu", "trainer.cu", "tc_model.cu", "mlp_tc256.cu",
            "serve.cpp", "noalloc.cu", "tune.cu", "update.cpp", "hybrid.cpp",
            "selftest.cu"]
 HEADERS = ["internal.h", "search_dev.cuh", "tc_ptx.cuh", "tc_common.cuh"]

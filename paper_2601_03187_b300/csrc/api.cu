@@ -39,6 +39,21 @@ int ctx_alloc(tang_ctx *ctx, size_t bytes, void **p) {
     return TANG_OK;
 }
 
+int ctx_try_alloc(tang_ctx *ctx, size_t bytes, void **p) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    std::lock_guard<std::mutex> g(ctx->alloc_mu);
+    if (ctx->cap && ctx->used + bytes > ctx->cap) return TANG_ENOMEM;
+    if (cudaMalloc(p, bytes) != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return TANG_ENOMEM;
+    }
+    ctx->allocs[*p] = bytes;
+    ctx->used += bytes;
+    return TANG_OK;
+}
+
 void ctx_free(tang_ctx *ctx, void *p) {
     if (!p) return;
     std::lock_guard<std::mutex> g(ctx->alloc_mu);
@@ -102,14 +117,14 @@ int tang::check_device_error(tang_ctx *ctx) {
     return TANG_OK;
 }
 
-// Kernel variant requested by flag bits: 1 = 1-SM N=128, 2 = 2-SM pairs, 3 / 4 = 1-SM with weight
-// tiles multicast across clusters of 2 / 4 CTAs, 5 = 1-SM N=256, 0 = tuned or library default.
+// Search mode bits (search_dev.cuh) requested by TANG_SEARCH_* flags.
+int tang::search_mode_of(uint32_t flags) {
+    return ((flags & TANG_SEARCH_PAPER) ? 1 : 0) | ((flags & TANG_SEARCH_SERIAL) ? 2 : 0);
+}
+
+// Kernel variant requested by flag bits: 5 = the N=256 fused kernel, 0 = tuned or library default.
 static int variant_of(uint32_t flags) {
     if (flags & TANG_FUSED_N256) return 5;
-    if (flags & TANG_FUSED_2SM) return 2;
-    if (flags & TANG_FUSED_MCAST4) return 4;
-    if (flags & TANG_FUSED_MCAST2) return 3;
-    if (flags & TANG_FUSED_1SM) return 1;
     return 0;
 }
 
@@ -121,7 +136,7 @@ static Ruleset *find_rs(tang_ctx *ctx, uint32_t rs) {
 // Checked builds synchronise after every classify and search call (unless the stream is being
 // captured) and report the device error word, so that an index found out of range surfaces at the
 // call that formed it; other builds check it at the calls that synchronise anyway.
-static int checked_sync(tang_ctx *ctx, cudaStream_t st) {
+int tang::checked_sync(tang_ctx *ctx, cudaStream_t st) {
 #ifdef TANG_CHECKED
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone) {
@@ -133,6 +148,53 @@ static int checked_sync(tang_ctx *ctx, cudaStream_t st) {
     (void)st;
 #endif
     return TANG_OK;
+}
+
+void tang::note_classify(Ruleset &rs, cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+        cudaGetLastError();
+        return;  // work captured into a graph runs when the graph is launched, under the caller's ordering
+    }
+    std::lock_guard<std::mutex> g(rs.inflight_mu);
+    for (auto &e : rs.inflight)
+        if (e.first == st) {
+            cudaEventRecord(e.second, st);
+            return;
+        }
+    if (rs.inflight.size() >= 16) {
+        // forget streams whose last classification has completed
+        std::vector<std::pair<cudaStream_t, cudaEvent_t>> keep;
+        for (auto &e : rs.inflight) {
+            if (cudaEventQuery(e.second) == cudaSuccess)
+                cudaEventDestroy(e.second);
+            else
+                keep.push_back(e);
+        }
+        cudaGetLastError();
+        rs.inflight.swap(keep);
+    }
+    cudaEvent_t ev = nullptr;
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+        // no event: fall back to waiting here, so an update can never overtake this classification
+        cudaGetLastError();
+        cudaStreamSynchronize(st);
+        return;
+    }
+    cudaEventRecord(ev, st);
+    rs.inflight.emplace_back(st, ev);
+}
+
+int tang::wait_classifies(tang_ctx *ctx, Ruleset &rs, cudaStream_t st) {
+    std::lock_guard<std::mutex> g(rs.inflight_mu);
+    for (auto &e : rs.inflight) CK(cudaStreamWaitEvent(st, e.second, 0));
+    return TANG_OK;
+}
+
+static void free_inflight(Ruleset &rs) {
+    std::lock_guard<std::mutex> g(rs.inflight_mu);
+    for (auto &e : rs.inflight) cudaEventDestroy(e.second);
+    rs.inflight.clear();
 }
 
 int tang_checked_build(void) {
@@ -180,6 +242,10 @@ int tang_create(int device, size_t pool_bytes, tang_ctx **out) {
         tang_destroy(ctx);
         return TANG_ENOMEM;
     }
+    if (noalloc_prepare(ctx) != TANG_OK) {
+        tang_destroy(ctx);
+        return TANG_EDEVICE;
+    }
     *out = ctx;
     return TANG_OK;
 }
@@ -197,6 +263,7 @@ void tang_destroy(tang_ctx *ctx) {
         tss_free(ctx, *kv.second);
         if (kv.second->model) tang_model_free(ctx, kv.second->model.get());
         if (kv.second->last_update) cudaEventDestroy(kv.second->last_update);
+        free_inflight(*kv.second);
     }
     ctx->rulesets.clear();
     ctx_free(ctx, ctx->scratch);
@@ -254,6 +321,7 @@ int tang_unload_ruleset(tang_ctx *ctx, uint32_t rsh) {
     tss_free(ctx, *rs);
     if (rs->model) tang_model_free(ctx, rs->model.get());
     if (rs->last_update) cudaEventDestroy(rs->last_update);
+    free_inflight(*rs);
     ctx->rulesets.erase(rsh);
     return TANG_OK;
 }
@@ -319,10 +387,6 @@ void tang_model_free(tang_ctx *ctx, DeviceModel *m) {
     ctx_free(ctx, m->d_bias_tc);
     ctx_free(ctx, m->d_fold8);
     ctx_free(ctx, m->d_l0);
-    free(m->tmap_bf16);
-    free(m->tmap_fp8);
-    free(m->tmap2_bf16);
-    free(m->tmap2_fp8);
     free(m->tmap256);
     m->d_params = nullptr;
 }
@@ -460,7 +524,7 @@ static int run_infer(tang_ctx *ctx, Ruleset &rs, const tang_header *h, uint32_t 
 
 // Enqueue the device-resident classification of one batch on `st` (no synchronisation).
 static int enqueue_classify(tang_ctx *ctx, Ruleset &rs, const tang_header *h, uint32_t n, uint32_t *ids,
-                            uint32_t path, DevStats *stats, cudaStream_t st, int variant = 0, bool paper = false) {
+                            uint32_t path, DevStats *stats, cudaStream_t st, int variant = 0, int smode = 0) {
     if (n == 0) return TANG_OK;
     const int cw = int(rs.host.cw);
     const TuneEntry *tune = nullptr;
@@ -469,7 +533,7 @@ static int enqueue_classify(tang_ctx *ctx, Ruleset &rs, const tang_header *h, ui
     switch (path) {
         case TANG_PATH_NO_NN: {
             cudaError_t e = launch_search(rs.d_desc, uint32_t(rs.host.tuples.size()), cw, h, nullptr, n, ids, stats,
-                                          tune, st, paper);
+                                          tune, st, smode);
             if (e != cudaSuccess) return set_err(ctx, TANG_EDEVICE, "search: %s", cudaGetErrorString(e));
             return TANG_OK;
         }
@@ -493,7 +557,7 @@ static int enqueue_classify(tang_ctx *ctx, Ruleset &rs, const tang_header *h, ui
                 rc = run_infer(ctx, rs, h + c0, rows, nullptr, tup, prec, st, variant);
                 if (rc) return rc;
                 cudaError_t e = launch_search(rs.d_desc, uint32_t(rs.host.tuples.size()), cw, h + c0, tup, rows,
-                                              ids + c0, stats, tune, st, paper);
+                                              ids + c0, stats, tune, st, smode);
                 if (e != cudaSuccess) return set_err(ctx, TANG_EDEVICE, "search: %s", cudaGetErrorString(e));
             }
             return TANG_OK;
@@ -505,7 +569,7 @@ static int enqueue_classify(tang_ctx *ctx, Ruleset &rs, const tang_header *h, ui
             const int prec = path == TANG_PATH_FUSED_BF16 ? TANG_BF16 : TANG_FP8;
             if (prec == TANG_FP8 && !rs.model->has_fp8)
                 return set_err(ctx, TANG_EINVAL, "FP8 path needs a calibrated model (act_amax)");
-            return tc_launch(ctx, rs, h, n, ids, nullptr, nullptr, prec, true, stats, st, tune, variant, paper);
+            return tc_launch(ctx, rs, h, n, ids, nullptr, nullptr, prec, true, stats, st, tune, variant, smode);
         }
         default:
             return set_err(ctx, TANG_EINVAL, "unknown path %u", path);
@@ -513,7 +577,7 @@ static int enqueue_classify(tang_ctx *ctx, Ruleset &rs, const tang_header *h, ui
 }
 
 static int classify_host(tang_ctx *ctx, Ruleset &rs, const tang_header *h, uint32_t n, uint32_t *ids, uint32_t path,
-                         DevStats *stats, int variant, bool paper);
+                         DevStats *stats, int variant, int smode);
 
 
 int tang_classify(tang_ctx *ctx, uint32_t rsh, const tang_header *headers, uint32_t n, uint32_t *ids, uint32_t flags,
@@ -527,30 +591,30 @@ int tang_classify(tang_ctx *ctx, uint32_t rsh, const tang_header *headers, uint3
         return set_err(ctx, TANG_EINVAL, "headers must be 16-byte aligned and ids 4-byte aligned");
     const uint32_t path = flags & TANG_PATH_MASK;
     const int variant = variant_of(flags);
-    const bool paper = (flags & TANG_SEARCH_PAPER) != 0;
+    const int smode = search_mode_of(flags);
     cudaSetDevice(ctx->device);
     cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : ctx->stream;
     DevStats *dst = stats ? ctx->d_stats : nullptr;
     if (dst) CK(cudaMemsetAsync(dst, 0, sizeof(DevStats), st));
     int rc;
     if (flags & TANG_MEM_HOST) {
-        rc = classify_host(ctx, *rs, headers, n, ids, path, dst, variant, paper);
+        rc = classify_host(ctx, *rs, headers, n, ids, path, dst, variant, smode);
     } else {
         if (rs->has_update) CK(cudaStreamWaitEvent(st, rs->last_update, 0));
         if ((flags & TANG_GRAPH) && !dst && n) {
-            GraphKey key{rsh, path | uint32_t(variant) << 8 | uint32_t(paper) << 16, n, headers, ids, (void *)st};
+            GraphKey key{rsh, path | uint32_t(variant) << 8 | uint32_t(smode) << 16, n, headers, ids, (void *)st};
             auto it = ctx->graphs.find(key);
             if (it == ctx->graphs.end()) {
                 // First call for this key: run eagerly (this sizes any scratch, so nothing
                 // allocates or synchronises inside the capture), then capture for later calls.
-                rc = enqueue_classify(ctx, *rs, headers, n, ids, path, nullptr, st, variant, paper);
+                rc = enqueue_classify(ctx, *rs, headers, n, ids, path, nullptr, st, variant, smode);
                 if (rc) return rc;
                 CK(cudaStreamSynchronize(st));
                 // capture on a private stream so the caller's stream may be the legacy one
                 cudaStream_t cap;
                 CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
                 CK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
-                rc = enqueue_classify(ctx, *rs, headers, n, ids, path, nullptr, cap, variant, paper);
+                rc = enqueue_classify(ctx, *rs, headers, n, ids, path, nullptr, cap, variant, smode);
                 cudaGraph_t g = nullptr;
                 cudaError_t e = cudaStreamEndCapture(cap, &g);
                 cudaStreamDestroy(cap);
@@ -569,8 +633,9 @@ int tang_classify(tang_ctx *ctx, uint32_t rsh, const tang_header *headers, uint3
             }
             rc = TANG_OK;
         } else {
-            rc = enqueue_classify(ctx, *rs, headers, n, ids, path, dst, st, variant, paper);
+            rc = enqueue_classify(ctx, *rs, headers, n, ids, path, dst, st, variant, smode);
         }
+        if (rc == TANG_OK && n) note_classify(*rs, st);
     }
     if (rc) return rc;
     if (stats) {
@@ -594,7 +659,7 @@ int tang_classify(tang_ctx *ctx, uint32_t rsh, const tang_header *headers, uint3
 // D2H (copy_out stream) through two device buffers, so copies of one chunk overlap the
 // compute of the next. Pageable user buffers are staged through pinned buffers by this thread.
 static int classify_host(tang_ctx *ctx, Ruleset &rs, const tang_header *h, uint32_t n, uint32_t *ids, uint32_t path,
-                         DevStats *stats, int variant, bool paper) {
+                         DevStats *stats, int variant, int smode) {
     if (n == 0) return TANG_OK;
     const uint32_t chunk = std::min<uint32_t>(n, 1u << 20);
     if (ctx->dev_pkts < chunk) {
@@ -660,7 +725,7 @@ static int classify_host(tang_ctx *ctx, Ruleset &rs, const tang_header *h, uint3
         cudaEventRecord(ev_in[b], ctx->copy_in);
         cudaStreamWaitEvent(ctx->stream, ev_in[b], 0);
         rc = enqueue_classify(ctx, rs, dh + size_t(b) * chunk, rows, di + size_t(b) * chunk, path, stats, ctx->stream,
-                              variant, paper);
+                              variant, smode);
         cudaEventRecord(ev_comp[b], ctx->stream);
         cudaStreamWaitEvent(ctx->copy_out, ev_comp[b], 0);
         uint32_t *dst = pinned ? ids + c0 : pi + size_t(b) * chunk;
@@ -718,9 +783,11 @@ int tang_search_ex(tang_ctx *ctx, uint32_t rsh, const tang_header *d_headers, co
     if (rs->has_update) CK(cudaStreamWaitEvent(st, rs->last_update, 0));
     DevStats *dst = stats ? ctx->d_stats : nullptr;
     if (dst) CK(cudaMemsetAsync(dst, 0, sizeof(DevStats), st));
-    if (flags & ~uint32_t(TANG_SEARCH_PAPER)) return set_err(ctx, TANG_EINVAL, "unknown search flags 0x%x", flags);
+    if (flags & ~uint32_t(TANG_SEARCH_PAPER | TANG_SEARCH_SERIAL))
+        return set_err(ctx, TANG_EINVAL, "unknown search flags 0x%x", flags);
     CK(launch_search(rs->d_desc, uint32_t(rs->host.tuples.size()), rs->host.cw, d_headers, d_tuple, n, d_ids, dst,
-                     nullptr, st, (flags & TANG_SEARCH_PAPER) != 0));
+                     nullptr, st, search_mode_of(flags)));
+    if (n) note_classify(*rs, st);
     if (stats) {
         DevStats hs;
         CK(cudaMemcpyAsync(&hs, dst, sizeof(hs), cudaMemcpyDeviceToHost, st));
@@ -737,7 +804,9 @@ int tang_insert_rule(tang_ctx *ctx, uint32_t rsh, const tang_rule *rule) {
     Ruleset *rs = find_rs(ctx, rsh);
     if (!rs) return set_err(ctx, TANG_ENOTFOUND, "unknown ruleset %u", rsh);
     cudaSetDevice(ctx->device);
-    int rc = tss_insert(ctx, *rs, *rule, ctx->stream);
+    // classifications already issued on other streams read the tables this call rewrites in place
+    int rc = wait_classifies(ctx, *rs, ctx->stream);
+    if (!rc) rc = tss_insert(ctx, *rs, *rule, ctx->stream);
     if (rc) return rc;
     CK(cudaEventRecord(rs->last_update, ctx->stream));
     rs->has_update = true;
@@ -750,7 +819,8 @@ int tang_delete_rule(tang_ctx *ctx, uint32_t rsh, uint32_t id) {
     Ruleset *rs = find_rs(ctx, rsh);
     if (!rs) return set_err(ctx, TANG_ENOTFOUND, "unknown ruleset %u", rsh);
     cudaSetDevice(ctx->device);
-    int rc = tss_delete(ctx, *rs, id, ctx->stream);
+    int rc = wait_classifies(ctx, *rs, ctx->stream);
+    if (!rc) rc = tss_delete(ctx, *rs, id, ctx->stream);
     if (rc) return rc;
     CK(cudaEventRecord(rs->last_update, ctx->stream));
     rs->has_update = true;
@@ -778,7 +848,9 @@ int enqueue_classify_path(tang_ctx *ctx, uint32_t rsh, const tang_header *h, uin
     Ruleset *rs = find_rs(ctx, rsh);
     if (!rs) return set_err(ctx, TANG_ENOTFOUND, "unknown ruleset %u", rsh);
     if (rs->has_update) CK(cudaStreamWaitEvent(st, rs->last_update, 0));
-    return enqueue_classify(ctx, *rs, h, n, ids, path, nullptr, st);
+    const int rc = enqueue_classify(ctx, *rs, h, n, ids, path, nullptr, st);
+    if (rc == TANG_OK && n) note_classify(*rs, st);
+    return rc;
 }
 void drop_graphs_of(tang_ctx *ctx) { drop_graphs(ctx); }
 }  // namespace tang

@@ -152,11 +152,7 @@ struct DeviceModel {
     float act_amax[64] = {0};
     bool has_fp8 = false;
     float act_scale[64] = {0};        // FP8 activation scale per tensor-core layer input
-    void *tmap_bf16 = nullptr;        // host-side CUtensorMap pairs, see tc_common.cuh (1-SM kernel)
-    void *tmap_fp8 = nullptr;
-    void *tmap2_bf16 = nullptr;       // half-tile maps of the 2-SM kernel
-    void *tmap2_fp8 = nullptr;
-    void *tmap256 = nullptr;          // 256-row maps of the N=256 kernel: [BF16, FP8]
+    void *tmap256 = nullptr;          // host-side tensor maps of the fused kernel: [BF16, FP8]
 };
 
 struct Ruleset;
@@ -175,7 +171,7 @@ struct TuneEntry {
     int search_threads = 0;  // threads per block of the search kernel (128 / 256 / 512)
     int search_bps = 0;      // resident blocks per SM the search grid is sized for
     int fused_grid = 0;      // persistent CTAs of the fused kernel (0 = one per SM)
-    int fused_variant = 0;   // 0 = library default, 1 = N=128 1-SM, 2 = 2-SM pairs, 3 / 4 = clusters, 5 = N=256
+    int fused_variant = 0;   // 0 = library default, 5 = the N=256 fused kernel
     float ms = 0.f;          // best time measured by the tuner
 };
 
@@ -196,6 +192,10 @@ struct Ruleset {
     std::unique_ptr<DeviceModel> model;
     cudaEvent_t last_update = nullptr;  // classify waits on it
     bool has_update = false;
+    // One event per stream that has classified against this ruleset, recorded after its latest
+    // classification: an update waits for all of them before it touches the tables.
+    std::mutex inflight_mu;
+    std::vector<std::pair<cudaStream_t, cudaEvent_t>> inflight;
     double build_ms = 0;
     std::map<uint32_t, TuneEntry> tune;  // per path
     // deferred-update monitor (§5.2.2): the open window's packets and cost, and the throughput of
@@ -234,6 +234,7 @@ struct tang_ctx {
     size_t dev_pkts = 0;
     int sm_count = 148;
     tang::ServeEngine *serve = nullptr;
+    int32_t *noalloc_tuples = nullptr;  // device address of tang_classify_noalloc's static array
 };
 
 // ---------------------------------------------------------------------------------------
@@ -245,8 +246,19 @@ int set_err(tang_ctx *ctx, int code, const char *fmt, ...);
 // wait ran out since the last check, else TANG_OK.
 int check_device_error(tang_ctx *ctx);
 int ctx_alloc(tang_ctx *ctx, size_t bytes, void **p);
+// ctx_alloc without touching the context's error text (for the serving engine's own thread).
+int ctx_try_alloc(tang_ctx *ctx, size_t bytes, void **p);
 void ctx_free(tang_ctx *ctx, void *p);
 int ensure_scratch(tang_ctx *ctx, size_t bytes);
+// Checked builds: synchronise `st` (unless it is being captured) and report the device error word.
+int checked_sync(tang_ctx *ctx, cudaStream_t st);
+// Record, on `st`, that a classification against `rs` was enqueued there (no-op while `st` is
+// being captured into a graph).
+void note_classify(Ruleset &rs, cudaStream_t st);
+// Make `st` wait for every classification noted against `rs` (before an update of its tables).
+int wait_classifies(tang_ctx *ctx, Ruleset &rs, cudaStream_t st);
+// noalloc.cu: resolve the device address of the no-alloc scratch array for ctx->device.
+int noalloc_prepare(tang_ctx *ctx);
 
 // tss_host.cpp
 int tss_build(tang_ctx *ctx, Ruleset &rs, const tang_rule *rules, uint32_t n);
@@ -258,7 +270,8 @@ int tss_rebuild(tang_ctx *ctx, Ruleset &rs, bool &same_tuples);
 int tss_set_pool_view(tang_ctx *ctx, Ruleset &rs, uint32_t n);
 uint64_t fmix64_host(uint64_t k);
 
-// search.cu
+// search.cu (mode: search_dev.cuh's kSearchPaper / kSearchSerial bits, from the TANG_SEARCH_* flags)
+int search_mode_of(uint32_t flags);
 cudaError_t launch_conflict_build(const DRule *sorted, const uint32_t *sorted_pos, uint32_t n, DRule *pool,
                                   uint32_t *cwords, uint32_t cw, uint32_t T, cudaStream_t st);
 cudaError_t launch_conflict_insert(const Tables *d_desc, uint32_t pool_size, uint32_t new_pos, uint32_t cw,
@@ -267,7 +280,7 @@ cudaError_t launch_run_shift(DRule *pool, uint32_t start, uint32_t len, uint32_t
 cudaError_t launch_run_copy(DRule *pool, uint32_t from, uint32_t to, uint32_t len, cudaStream_t st);
 cudaError_t launch_search(const Tables *d_desc, uint32_t T, uint32_t cw, const tang_header *h,
                           const int32_t *tuple, uint32_t n, uint32_t *ids, DevStats *stats, const TuneEntry *tune,
-                          cudaStream_t st, bool paper = false);
+                          cudaStream_t st, int mode = 0);
 
 // mlp_simt.cu (FP32 CUDA-core kernels: plain path and trainer)
 cudaError_t launch_encode(const tang_header *h, uint32_t n, float *X, uint32_t ldx, float scale, cudaStream_t st);
@@ -278,12 +291,11 @@ cudaError_t launch_argmax(const float *Z, int ldz, int n, int C, int32_t *out, c
 int mlp_fp32_forward(tang_ctx *ctx, const DeviceModel &m, const tang_header *h, uint32_t n, float *logits,
                      int32_t *tuple, cudaStream_t st);
 
-// mlp_tc.cu (tcgen05 fused kernels)
+// tc_model.cu (host side of the tcgen05 fused kernel in mlp_tc256.cu)
 int tc_prepare_model(tang_ctx *ctx, DeviceModel &m);
 int tc_launch(tang_ctx *ctx, Ruleset &rs, const tang_header *h, uint32_t n, uint32_t *ids, float *logits,
               int32_t *tuple, int precision, bool fused_search, DevStats *stats, cudaStream_t st,
-              const TuneEntry *tune, int variant, bool paper = false);
-int tc2_prepare_model(tang_ctx *ctx, DeviceModel &m);
+              const TuneEntry *tune, int variant, int mode = 0);
 int tc256_prepare_model(tang_ctx *ctx, DeviceModel &m);
 
 // trainer.cu; init != nullptr starts from that model's parameters (incremental training)

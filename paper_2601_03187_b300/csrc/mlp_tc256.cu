@@ -628,7 +628,7 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
                     // headers and ids stream through L2 with evict-first hints, the tables stay
                     const Hdr h = load_header_stream(p.headers + i);
                     Best best;
-                    const bool hit = search_packet(tb, tb.tuples, tb.order, h, pred, best, cn, (p.fused_search & 2) != 0);
+                    const bool hit = search_packet(tb, tb.tuples, tb.order, h, pred, best, cn, p.fused_search >> 1);
                     __stcs(p.ids + i, best.id);
                     if (p.stats) {
                         st_pk++;

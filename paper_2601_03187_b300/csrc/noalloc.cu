@@ -7,34 +7,27 @@
 // hook, a process whose device memory is fixed up front, or a latency-bound loop that cannot
 // accept cudaMalloc's implicit device synchronisation. tang_classify_noalloc serves them by
 // passing the predictions through the file-scope device array below instead.
-#include <mutex>
-
 #include "internal.h"
 
 namespace tang {
 
-// One int32 predicted tuple per packet of the largest allowed batch (4 MiB). Every GPU that
-// loads the library holds this array until the process exits. All calls share it.
+// One int32 predicted tuple per packet of the largest allowed batch (4 MiB). It is part of this
+// library's device module: a GPU holds it from the moment the module is loaded on it (at the
+// latest when a context is created there, see noalloc_prepare) until the process exits. All
+// calls and contexts on a device share it.
 static __device__ __align__(256) int32_t g_noalloc_tuples[TANG_NOALLOC_MAX_PACKETS];
 
-// Device address of g_noalloc_tuples, looked up once per device (with that device current).
-// In host code the symbol's name is only a host-side stand-in, never a device address.
-static std::mutex g_noalloc_mu;
-static int32_t *g_noalloc_ptr[64];
-static bool g_noalloc_ready[64];
-
-static int noalloc_scratch(tang_ctx *ctx, int32_t **out) {
-    if (ctx->device < 0 || ctx->device >= 64) return set_err(ctx, TANG_EUNSUPPORTED, "device index >= 64");
-    std::lock_guard<std::mutex> g(g_noalloc_mu);
-    if (!g_noalloc_ready[ctx->device]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_tuples);
-        if (e != cudaSuccess || !p)
-            return set_err(ctx, TANG_EDEVICE, "cudaGetSymbolAddress(no-alloc scratch): %s", cudaGetErrorString(e));
-        g_noalloc_ptr[ctx->device] = static_cast<int32_t *>(p);
-        g_noalloc_ready[ctx->device] = true;
+// Called by tang_create with the context's device current: looks up the array's device address
+// once per context, so that the entry point itself never loads a module or allocates. In host
+// code the symbol's name is only a host-side stand-in, never a device address.
+int noalloc_prepare(tang_ctx *ctx) {
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_tuples);
+    if (e != cudaSuccess || !p) {
+        cudaGetLastError();
+        return set_err(ctx, TANG_EDEVICE, "cudaGetSymbolAddress(no-alloc scratch): %s", cudaGetErrorString(e));
     }
-    *out = g_noalloc_ptr[ctx->device];
+    ctx->noalloc_tuples = static_cast<int32_t *>(p);
     return TANG_OK;
 }
 
@@ -54,21 +47,22 @@ extern "C" int tang_classify_noalloc(tang_ctx *ctx, uint32_t rsh, const tang_hea
     if (n == 0) return TANG_OK;
     if (!d_headers || !d_ids || (reinterpret_cast<uintptr_t>(d_headers) & 15) || (reinterpret_cast<uintptr_t>(d_ids) & 3))
         return set_err(ctx, TANG_EINVAL, "headers must be 16-byte aligned device memory and ids 4-byte aligned");
-    if (!rs.model || !rs.model->d_wbf16 || !rs.model->tmap_bf16)
-        return set_err(ctx, TANG_EINVAL, "ruleset %u has no tensor-core model", rsh);
+    if (!rs.model) return set_err(ctx, TANG_EINVAL, "ruleset %u has no model", rsh);
+    if (!rs.model->d_wbf16)
+        return set_err(ctx, TANG_EUNSUPPORTED, "tensor-core path needs N == 256 or 512 and 1 <= blocks <= 31");
+    if (!ctx->noalloc_tuples) return set_err(ctx, TANG_EDEVICE, "no-alloc scratch address unknown");
     if (cudaSetDevice(ctx->device) != cudaSuccess) return set_err(ctx, TANG_EDEVICE, "cudaSetDevice failed");
-    int32_t *tuples = nullptr;
-    int rc = noalloc_scratch(ctx, &tuples);
-    if (rc) return rc;
     cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : ctx->stream;
     if (rs.has_update && cudaStreamWaitEvent(st, rs.last_update, 0) != cudaSuccess)
         return set_err(ctx, TANG_EDEVICE, "cudaStreamWaitEvent failed");
     // every entry below n is written by the network kernel before the search kernel reads it,
     // so the array needs no clearing between calls
-    rc = tc_launch(ctx, rs, d_headers, n, nullptr, nullptr, tuples, TANG_BF16, false, nullptr, st, nullptr, 0);
+    int rc = tc_launch(ctx, rs, d_headers, n, nullptr, nullptr, ctx->noalloc_tuples, TANG_BF16, false, nullptr, st,
+                       nullptr, 0);
     if (rc) return rc;
-    cudaError_t e = launch_search(rs.d_desc, uint32_t(rs.host.tuples.size()), rs.host.cw, d_headers, tuples, n, d_ids,
-                                  nullptr, nullptr, st);
+    cudaError_t e = launch_search(rs.d_desc, uint32_t(rs.host.tuples.size()), rs.host.cw, d_headers,
+                                  ctx->noalloc_tuples, n, d_ids, nullptr, nullptr, st);
     if (e != cudaSuccess) return set_err(ctx, TANG_EDEVICE, "search: %s", cudaGetErrorString(e));
-    return TANG_OK;
+    note_classify(rs, st);
+    return checked_sync(ctx, st);
 }

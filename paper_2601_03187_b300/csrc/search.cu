@@ -17,7 +17,7 @@ __device__ __forceinline__ void warp_add(unsigned long long *dst, uint32_t v) {
 template <int THREADS, bool STATS>
 __global__ void __launch_bounds__(THREADS) k_search(const Tables *__restrict__ desc, const tang_header *__restrict__ hdr,
                                                 const int32_t *__restrict__ pred, uint32_t n,
-                                                uint32_t *__restrict__ ids, DevStats *stats, bool paper) {
+                                                uint32_t *__restrict__ ids, DevStats *stats, int mode) {
     __shared__ TupleDesc s_tuples[kSmemTuples];
     __shared__ uint16_t s_order[kSmemTuples];
     const Tables tb = *desc;
@@ -39,7 +39,7 @@ __global__ void __launch_bounds__(THREADS) k_search(const Tables *__restrict__ d
         const Hdr h = load_header(hdr + i);
         const int p = pred ? __ldg(pred + i) : -1;
         Best best;
-        const bool hit = search_packet(tb, tuples, order, h, p, best, c, paper);
+        const bool hit = search_packet(tb, tuples, order, h, p, best, c, mode);
         ids[i] = best.id;
         if (STATS) {
             st_pk++;
@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(THREADS) k_search(const Tables *__restrict__ d
 
 cudaError_t launch_search(const Tables *d_desc, uint32_t T, uint32_t cw, const tang_header *h, const int32_t *tuple,
                           uint32_t n, uint32_t *ids, DevStats *stats, const TuneEntry *tune, cudaStream_t st,
-                          bool paper) {
+                          int mode) {
     (void)T;
     (void)cw;
     if (n == 0) return cudaSuccess;
@@ -78,9 +78,9 @@ cudaError_t launch_search(const Tables *d_desc, uint32_t T, uint32_t cw, const t
     if (blocks > cap) blocks = cap;
 #define TANG_SEARCH_LAUNCH(TH)                                                                     \
     if (stats)                                                                                     \
-        k_search<TH, true><<<blocks, TH, 0, st>>>(d_desc, h, tuple, n, ids, stats, paper);                 \
+        k_search<TH, true><<<blocks, TH, 0, st>>>(d_desc, h, tuple, n, ids, stats, mode);                 \
     else                                                                                           \
-        k_search<TH, false><<<blocks, TH, 0, st>>>(d_desc, h, tuple, n, ids, stats, paper);
+        k_search<TH, false><<<blocks, TH, 0, st>>>(d_desc, h, tuple, n, ids, stats, mode);
     if (threads == 128) {
         TANG_SEARCH_LAUNCH(128)
     } else if (threads == 512) {

@@ -1,5 +1,5 @@
 // Device functions of the exact tuple-space search (stage 2 of §5.1.1), shared by the staged
-// search kernel (search.cu) and the fused classification kernel (mlp_tc.cu).
+// search kernel (search.cu) and the fused classification kernel (mlp_tc256.cu).
 #pragma once
 
 #include "internal.h"
@@ -71,11 +71,70 @@ struct Counters {
     uint32_t probes, rule_reads, slot_reads;
 };
 
+// Runs longer than this are scanned by the lanes of the warp together (scan_run_coop).
+constexpr uint32_t kCoopRun = 16;
+
+// Scan the runs of every lane of the calling group (the lanes that are executing this call
+// together) cooperatively: for each member's run in turn, the group reads consecutive rules of it
+// in one coalesced step per group size (lane of rank k takes rule base + k), and two ballots find
+// the first rule in run order that matches or that no longer beats the member's current best (the
+// run is priority-sorted, so the scan ends there). Each lane gets its own run's outcome: the
+// same rule, the same improvement of `best` and the same count of rule reads as a serial scan.
+// Control flow is uniform across the group, so every shuffle and ballot sees all its lanes.
+__device__ __forceinline__ bool scan_run_coop(const Tables &tb, uint32_t run_start, uint32_t run_len, uint32_t t,
+                                           const Hdr &h, Best &best, Counters &c) {
+    const uint32_t grp = __activemask();
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t rank = __popc(grp & ((1u << lane) - 1u));
+    const uint32_t g = __popc(grp);
+    bool mine = false;
+    for (uint32_t pending = grp; pending; pending &= pending - 1) {
+        const int leader = __ffs(pending) - 1;
+        const uint32_t start = __shfl_sync(grp, run_start, leader), len = __shfl_sync(grp, run_len, leader);
+        const Hdr hl{__shfl_sync(grp, h.sip, leader), __shfl_sync(grp, h.dip, leader), __shfl_sync(grp, h.sp, leader),
+                     __shfl_sync(grp, h.dp, leader), __shfl_sync(grp, h.proto, leader)};
+        const uint32_t bprio = __shfl_sync(grp, best.prio, leader), bid = __shfl_sync(grp, best.id, leader);
+        uint32_t reads = len, found = kEmpty;  // found: run index of the matching rule
+        for (uint32_t base = 0; base < len; base += g) {
+            const uint32_t j = base + rank;
+            bool stop = false, match = false;
+            DRule r{};
+            if (j < len) {
+                if (TANG_INDEX_OK(tb, start + j < tb.pool_size)) {
+                    r = load_rule(tb.rules + start + j);
+                    stop = !(r.prio < bprio || (r.prio == bprio && r.id < bid));
+                    match = !stop && rule_match(r, hl);
+                } else {
+                    stop = true;  // checked build: index out of range, the access is skipped
+                }
+            }
+            const uint32_t ev = __ballot_sync(grp, stop || match);
+            if (ev) {
+                const int first = __ffs(ev) - 1;  // lowest lane = lowest rank = earliest rule
+                const uint32_t jf = base + __popc(grp & ((1u << first) - 1u));
+                reads = jf + 1;
+                if (__shfl_sync(grp, uint32_t(match), first)) {
+                    found = jf;
+                    const uint32_t fprio = __shfl_sync(grp, r.prio, first), fid = __shfl_sync(grp, r.id, first),
+                                   fcf = __shfl_sync(grp, r.cf, first);
+                    if (int(lane) == leader) best = Best{fprio, fid, start + jf, fcf, t};
+                }
+                break;
+            }
+        }
+        if (int(lane) == leader) {
+            c.rule_reads += reads;
+            mine = found != kEmpty;
+        }
+    }
+    return mine;
+}
+
 // Probe tuple t with the header truncated to the tuple's lengths (§4.3); scan the run under
 // that key in (priority, id) order and stop at the first match or at the first rule that does
 // not beat the current best. Returns true if `best` improved.
 __device__ __forceinline__ bool probe_tuple(const Tables &tb, const TupleDesc &d, uint32_t t, const Hdr &h,
-                                            Best &best, Counters &c) {
+                                            Best &best, Counters &c, bool coop) {
     const uint32_t ks = h.sip & d.mask_s, kd = h.dip & d.mask_d;
     const uint32_t start = uint32_t(fmix64((uint64_t(ks) << 32) | kd)) & d.slot_mask;
     for (uint32_t i = 0; i <= d.max_probe; ++i) {
@@ -85,6 +144,7 @@ __device__ __forceinline__ bool probe_tuple(const Tables &tb, const TupleDesc &d
         c.slot_reads++;
         if (s.z == kEmpty) return false;
         if (s.x == ks && s.y == kd) {
+            if (coop && s.w > kCoopRun) return scan_run_coop(tb, s.z, s.w, t, h, best, c);
             for (uint32_t j = 0; j < s.w; ++j) {
                 if (!TANG_INDEX_OK(tb, s.z + j < tb.pool_size)) return false;
                 DRule r = load_rule(tb.rules + s.z + j);
@@ -103,17 +163,21 @@ __device__ __forceinline__ bool probe_tuple(const Tables &tb, const TupleDesc &d
 
 // Full exact search of one header. `tuples` / `order` may point to shared-memory copies.
 // pred outside [0, T) means "no prediction". Returns true if the predicted tuple held a match.
-// paper: the post-verification exactly as §5.1.1 states it, kept for measurement: a match in the
-// predicted tuple is returned without the conflict-set probes (so it may be a lower-priority rule,
-// the uncorrected case of §5.1.1 and §8); a miss still searches the remaining tuples in order.
+// mode bit kSearchPaper: the post-verification exactly as §5.1.1 states it, kept for measurement:
+// a match in the predicted tuple is returned without the conflict-set probes (so it may be a
+// lower-priority rule, the uncorrected case of §5.1.1 and §8); a miss still searches the remaining
+// tuples in order. Bit kSearchSerial: every run is scanned by its own thread (no cooperative scan
+// of long runs), for measurement; the result is the same.
+constexpr int kSearchPaper = 1, kSearchSerial = 2;
 __device__ __forceinline__ bool search_packet(const Tables &tb, const TupleDesc *tuples, const uint16_t *order,
-                                              const Hdr &h, int pred, Best &best, Counters &c, bool paper = false) {
+                                              const Hdr &h, int pred, Best &best, Counters &c, int mode = 0) {
     const uint32_t T = tb.T;
+    const bool paper = (mode & kSearchPaper) != 0, coop = (mode & kSearchSerial) == 0;
     best = Best{0xFFFFFFFFu, 0xFFFFFFFFu, kEmpty, 0u, 0u};
     bool hit = false;
     if (uint32_t(pred) < T) {
         c.probes++;
-        hit = probe_tuple(tb, tuples[pred], uint32_t(pred), h, best, c);
+        hit = probe_tuple(tb, tuples[pred], uint32_t(pred), h, best, c, coop);
         if (hit && paper) return true;
     }
     // After a hit r: only tuples in conflict(r) can hold a better match. After a miss: all.
@@ -139,7 +203,7 @@ __device__ __forceinline__ bool search_packet(const Tables &tb, const TupleDesc 
         // tuples come in ascending best (priority, id): none from here on can win
         if (!beats(d.min_prio, d.min_id, best)) break;
         c.probes++;
-        probe_tuple(tb, d, t, h, best, c);
+        probe_tuple(tb, d, t, h, best, c, coop);
     }
     return hit;
 }

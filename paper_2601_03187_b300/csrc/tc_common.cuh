@@ -1,4 +1,4 @@
-// Pieces shared by the tensor-core kernels (1-SM and 2-SM variants).
+// Pieces shared by the tensor-core kernel (mlp_tc256.cu) and its host side (tc_model.cu).
 #pragma once
 
 #include <cuda.h>
@@ -18,14 +18,13 @@ struct TcParams {
     const Tables *tables;
     DevStats *stats;
     int *err;
-    const float *W0, *b0;   // FP32 layer 0: W0[7][512], b0[512]
-    const float *bias;      // [12][512] hidden biases, then [Cpad] output biases
+    const float *bias;      // [layers][N] hidden biases, then [Cpad] output biases
     const float *dq;        // FP8 only: per layer and output column 1 / (act scale * weight scale)
-    const float *sa;        // FP8 only: [13] activation scales of the layers' inputs
-    const float *fold8;     // FP8 only: [12][512] dq * s_out, then [12][512] bias * s_out (N=256 kernel)
+    const float *sa;        // FP8 only: [layers + 1] activation scales of the layers' inputs
+    const float *fold8;     // FP8 only: [layers][N] dq * s_out, then [layers][N] bias * s_out
     uint32_t C, Cpad;
-    uint32_t layers;        // N x N layers (2 x residual blocks); the N=128 kernels require 12
-    int fused_search;       // bit 0: run the search warps; bit 1: paper-mode post-verification
+    uint32_t layers;        // N x N layers (2 x residual blocks)
+    int fused_search;       // bit 0: run the search warps; bits 1-2: the search mode (search_packet)
     unsigned long long *trace;  // event timestamps of CTA 0 (trace builds only, else null)
 };
 
@@ -46,15 +45,7 @@ constexpr int kTotal = kEpiX + 2 * kChunks * 6;
     do {                                                                            \
         if (p.trace && blockIdx.x == 0 && (limit)) p.trace[(slot)] = clock64();     \
     } while (0)
-// 2-SM kernel: CTAs 0 and 1 (the first pair), each in its own kTotal-sized region
-#define TC_TRACE2(slot, limit)                                                                   \
-    do {                                                                                        \
-        if (p.trace && blockIdx.x < 2 && (limit)) p.trace[blockIdx.x * trace::kTotal + (slot)] = clock64(); \
-    } while (0)
 #else
-#define TC_TRACE2(slot, limit) \
-    do {                       \
-    } while (0)
 #define TC_TRACE(slot, limit) \
     do {                      \
     } while (0)
@@ -64,16 +55,6 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
     return *reinterpret_cast<uint32_t *>(&v);
 }
-__device__ __forceinline__ uint32_t pack_e4m3x4(float a, float b, float c, float d) {
-    const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(a, b), __NV_SATFINITE, __NV_E4M3);
-    const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(c, d), __NV_SATFINITE, __NV_E4M3);
-    return (lo & 0xFFFFu) | (hi << 16);
-}
-__device__ __forceinline__ float e4m3_to_f(uint32_t byte) {
-    __half_raw h = __nv_cvt_fp8_to_halfraw(__nv_fp8_storage_t(byte), __NV_E4M3);
-    return __half2float(__half(h));
-}
-
 // ReLU, round to nearest even and pack two BF16: lo in bits 0-15, hi in bits 16-31.
 __device__ __forceinline__ uint32_t relu_bf16x2(float lo, float hi) {
     uint32_t d;
@@ -92,10 +73,6 @@ __device__ __forceinline__ float2 e4m3x2_to_f2(uint32_t two) {
     asm("cvt.rn.f16x2.e4m3x2 %0, %1;" : "=r"(h2) : "h"(uint16_t(two & 0xFFFFu)));
     return __half22float2(*reinterpret_cast<const __half2 *>(&h2));
 }
-
-struct TcMaps {
-    CUtensorMap hid, out;
-};
 
 // Row-major [rows][cols] weight matrix of 1- or 2-byte elements as a TMA tensor map whose box is
 // 128 bytes x box_rows with 128-byte swizzle (cols * element size a multiple of 128).

@@ -1,9 +1,7 @@
 // Launch-shape autotuner: times the candidate launch shapes of a path on a caller-supplied
 // device batch and keeps the fastest per (ruleset, path). Candidates:
 //   search kernel (no-network, staged and plain paths): threads per block x blocks per SM;
-//   fused kernel: the tensor-core kernel variant (N=256; N=128 on one SM, on CTA pairs, or in
-//   clusters of 2 / 4 sharing weight tiles; the N=128 ones only for 6-block networks) and, for
-//   the N=256 kernel, the number of persistent CTAs (one per SM, or a divisor-friendly subset so
+//   fused kernel: the number of persistent CTAs (one per SM, or a divisor-friendly subset so
 //   that the tile count spreads evenly).
 #include <algorithm>
 
@@ -44,12 +42,6 @@ extern "C" int tang_autotune(tang_ctx *ctx, uint32_t rsh, const tang_header *d_h
             e.fused_grid = g;
             cands.push_back(e);
         }
-        if (rs.model->N == 512 && rs.model->layers == 12 && rs.model->C <= 128)  // the N=128 variants' limits
-            for (int v : {1, 2, 3, 4}) {
-                TuneEntry e;
-                e.fused_variant = v;
-                cands.push_back(e);
-            }
     } else {
         for (int th : {128, 256, 512})
             for (int bps : {2, 4, 8, 16}) {
@@ -105,13 +97,8 @@ extern "C" int tang_autotune_set(tang_ctx *ctx, uint32_t rsh, uint32_t path, int
     if (!ctx) return TANG_EINVAL;
     auto it = ctx->rulesets.find(rsh);
     if (it == ctx->rulesets.end()) return set_err(ctx, TANG_ENOTFOUND, "unknown ruleset %u", rsh);
-    const Ruleset &rs = *it->second;
-    if (variant < 0 || variant > 5 || grid < 0 || grid > ctx->sm_count)
+    if ((variant != 0 && variant != 5) || grid < 0 || grid > ctx->sm_count)
         return set_err(ctx, TANG_EINVAL, "variant %d / grid %d out of range", variant, grid);
-    if (variant >= 1 && variant <= 4 &&
-        !(rs.model && rs.model->N == 512 && rs.model->layers == 12 && rs.model->C <= 128))
-        return set_err(ctx, TANG_EINVAL, "variant %d needs a loaded 6-block, width-512 model of at most 128 classes",
-                       variant);
     const bool th_ok = search_threads == 0 || search_threads == 128 || search_threads == 256 || search_threads == 512;
     if (!th_ok || search_bps < 0 || search_bps > 16 || search_threads * search_bps > 2048)
         return set_err(ctx, TANG_EINVAL, "search launch %d threads x %d blocks per SM out of range", search_threads,

@@ -2,16 +2,18 @@
 512, 1-3 residual blocks, rulesets from tens to hundreds of tuples (one or several output
 chunks), batch sizes from one packet to several tiles per CTA, BF16 and FP8. Rule ids must equal
 the linear scan's, and the predicted tuple must be the first maximum of the logits the same
-call returns."""
+call returns; the logits of the first 4,096 packets must match the oracle's low-precision
+forward element by element, as in test_gpu_tc.py."""
 import numpy as np
 import pytest
 import torch
 
 import paper_2601_03187_b300 as tg
 import workloads as wl
-from gpu_util import ids_dev, ids_host, random_params, to_dev
+from gpu_util import calibrate, compare_logits, ids_dev, ids_host, random_params, to_dev
 from oracle import classify as oc
-from oracle import mlp, tss
+from oracle import mlp, mlp_lowp, tss
+from test_gpu_tc import PHI, PHI_TILE, RHO
 
 pytestmark = pytest.mark.gpu
 
@@ -39,13 +41,8 @@ def test_random_shapes_match_the_oracle(seed):
     blocks = int(rng.integers(1, 4))
     p = random_params(rng, N=width, blocks=blocks, C=T)
     calib = wl.gen_trace(rules, [("inside", 2048)], 3000 + seed)
-    p64 = {k: ([a.astype(np.float64) for a in v] if isinstance(v, list) else v.astype(np.float64)) for k, v in p.items()}
-    _, cache = mlp.forward(p64, mlp.features(calib), keep=True)
-    amax = []
-    for k in range(blocks):
-        amax += [np.abs(cache["h_in"][k]).max(), np.abs(cache["u"][k]).max()]
-    amax.append(np.abs(cache["h_out"]).max())
-    ctx.load_model(rs, tg.pack_model(p, np.array(amax, dtype=np.float32)))
+    amax = calibrate(p, mlp.features(calib))
+    ctx.load_model(rs, tg.pack_model(p, amax))
     n = int(rng.choice([1, 97, 128 * 148 + 5, 128 * 148 * 3 + 77]))
     h = wl.gen_trace(rules, [("inside", n - n // 8), ("random", n // 8)], 4000 + seed)
     want = oc.classify(rules, h)
@@ -62,4 +59,12 @@ def test_random_shapes_match_the_oracle(seed):
         zz = z.cpu().numpy()
         assert np.isfinite(zz).all()
         assert (t.cpu().numpy() == np.argmax(zz, axis=1)).all(), (seed, path)
+        m = min(n, 4096)
+        X = mlp.features(h[:m])
+        key = "bf16" if prec == tg.BF16 else "fp8"
+        z_or, mag = mlp_lowp.forward_bf16(p, X) if key == "bf16" else mlp_lowp.forward_fp8(p, X, amax)
+        stats, ok = compare_logits(zz[:m], z_or, mag, K=width, rho=RHO[key])
+        print(seed, width, blocks, T, n, key, stats)
+        assert ok and (m < 128 or stats["frac_tight"] >= PHI[key]), (seed, key, stats)
+        assert stats["min_tile_frac_tight"] is None or stats["min_tile_frac_tight"] >= PHI_TILE[key], (seed, key, stats)
     ctx.close()

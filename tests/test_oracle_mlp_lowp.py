@@ -141,3 +141,22 @@ def test_exact_networks_are_exact_in_fp32():
         # multiples of 2^-3, exact in sums below 2^21
         _check_exact(steps8, 2.0 ** -9, 2.0 ** 21)
         assert len(np.unique(z8)) > 100
+
+
+def test_logit_tolerance_is_below_the_logits_scale():
+    """The element-wise acceptance of the tensor-core tests (gpu_util.compare_logits with the RHO
+    of test_gpu_tc.py) allows less than 1 % (BF16) and 10 % (FP8) of each packet's largest |logit|,
+    on the networks those tests use."""
+    from gpu_util import calibrate, gamma
+    import ast
+    src = open(__file__.replace("test_oracle_mlp_lowp.py", "test_gpu_tc.py")).read()
+    rho = ast.literal_eval(src.split("RHO = ", 1)[1].split("\n", 1)[0])
+    rules = wl.rules_for_config(0)
+    X = mlp.features(wl.trace_for_config(0, rules, seed=5)[:2048])
+    p = random_params(np.random.default_rng(77), N=512, blocks=6, C=25)
+    amax = calibrate(p, X)
+    for prec, lim, (z, mag) in (("bf16", 0.01, mlp_lowp.forward_bf16(p, X)),
+                                ("fp8", 0.10, mlp_lowp.forward_fp8(p, X, amax))):
+        rowmax = np.abs(z).max(axis=1, keepdims=True)
+        tol = gamma(513) * mag + rho[prec] * rowmax
+        assert (tol / rowmax).max() < lim, (prec, float((tol / rowmax).max()))
