@@ -580,6 +580,61 @@ def cpu_model():
     return None
 
 
+def long_run_rules(n_plain, n_wild, seed):
+    """n_plain rules of the config-0 generator plus n_wild rules with both prefixes wildcarded
+    (one hash key of tuple (0,0): a run of n_wild+ rules) with exact ports and protocol that few
+    packets match, priorities interleaved at random: searches scan far into that run."""
+    rng = np.random.default_rng(seed)
+    plain = wl.gen_rules(n_plain, seed)
+    wild = wl.gen_rules(n_wild, seed + 1)
+    for f in ("sip", "dip"):
+        wild[f] = 0
+        wild[f + "_len"] = 0
+    for f in ("sp", "dp"):
+        v = rng.integers(0, 65536, n_wild)
+        wild[f + "_lo"] = v
+        wild[f + "_hi"] = v
+    wild["proto_wild"] = 0
+    wild["proto"] = 17
+    rules = np.concatenate([plain, wild])
+    rules["id"] = np.arange(len(rules))
+    rules["priority"] = rng.permutation(len(rules))
+    return rules
+
+
+def measure_long_runs(tg, ctx, n_packets=1 << 22):
+    """512k rules plus 8,192 rules under tuple (0,0) (one run of more than 8k rules under one key),
+    4M packets: the search alone and the fused BF16 path, each with the warp-cooperative scan of
+    long runs and with one thread per run (TANG_SEARCH_SERIAL); ids against the oracle."""
+    import torch
+    from oracle import classify as oc
+    rules = long_run_rules(N_RULES, 8192, 17)
+    rs = ctx.load_ruleset(rules)
+    quick_model(ctx, rs, rules, 18)
+    h = wl.gen_trace(rules, [("inside", n_packets // 2), ("zipf", n_packets // 2, 1.2)], 19)
+    d = torch.from_numpy(h.view(np.uint8).reshape(-1, 16)).cuda()
+    ids = torch.empty(len(h), dtype=torch.int32, device="cuda")
+    want = oc.classify(rules, h)
+    out = {"rules": len(rules), "run_00": int(((rules["sip_len"] == 0) & (rules["dip_len"] == 0)).sum()),
+           "packets": len(h)}
+    for path in ("no_nn", "fused_bf16"):
+        for serial in (False, True):
+            for _ in range(3):
+                ctx.classify(rs, d, ids, path=path, graph=True, serial=serial)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(5):
+                ctx.classify(rs, d, ids, path=path, graph=True, serial=serial)
+            torch.cuda.synchronize()
+            dt = (time.perf_counter() - t0) / 5
+            st = ctx.classify(rs, d, ids, path=path, stats=True, serial=serial)
+            out["%s_%s" % (path, "serial" if serial else "warp")] = {
+                "mpkts": round(len(h) / dt / 1e6, 3), "rule_reads_per_pkt": round(st["rule_reads"] / len(h), 3),
+                "ids_equal_oracle": bool((ids.cpu().numpy().view(np.uint32) == want).all())}
+    ctx.unload_ruleset(rs)
+    return out
+
+
 def argmax_flips(ctx, rs, d_h, n_tuples, chunk=1 << 22):
     """Precision-induced mispredictions: the share of packets whose predicted tuple (argmax of the
     network) under BF16 and under FP8 differs from the FP32 network's on the same batch. Rule ids
@@ -662,10 +717,14 @@ def main():
     ap.add_argument("--sizes", default="default", choices=sorted(MODEL_SHAPES),
                     help="network shapes of the model-size sweep (full: widths 64-512 x 1, 2, 3, 6 blocks)")
     ap.add_argument("--packets", type=int, default=N_PACKETS, help="use the first P packets of the trace")
+    ap.add_argument("--path", default="fused_bf16", choices=["fused_bf16", "fused_fp8"],
+                    help="the timed path of --quick runs (profiling one kernel); full runs time fused_bf16")
     ap.add_argument("--variant", default=None, choices=[None, "n256"],
                     help="tensor-core kernel variant (default: the library's choice)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
+    if not args.quick:
+        args.path = "fused_bf16"
     world, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, world, rank)
@@ -700,7 +759,7 @@ def main():
     # launch shapes picked by the library's autotuner on this batch (outside the timed region)
     tuned = {}
     if args.variant is None:
-        for path in ("fused_bf16",) if args.quick or world > 1 else ("fused_bf16", "fused_fp8"):
+        for path in (args.path,) if args.quick or world > 1 else ("fused_bf16", "fused_fp8"):
             ctx.autotune(rs, d_h, path=path)
             tuned[path] = ctx.autotune_get(rs, path)
 
@@ -720,11 +779,11 @@ def main():
 
     # ---- headline: fused BF16, graph-replayed
     with ClockSampler(local) as clk:
-        dt = time_path("fused_bf16", args.steps, args.warmup)
+        dt = time_path(args.path, args.steps, args.warmup)
     dt = max_over_ranks(dt, world)
     value = job_mpkts(n, args.steps, dt, world)
     ids_fused = ids.cpu().numpy().view(np.uint32)
-    st_bf16 = ctx.classify(rs, d_h, ids, path="fused_bf16", stats=True, variant=args.variant)
+    st_bf16 = ctx.classify(rs, d_h, ids, path=args.path, stats=True, variant=args.variant)
 
     fpp = flops_per_packet(T)
     ms_launch = dt / args.steps * 1e3
@@ -834,6 +893,7 @@ def main():
         if not args.no_du:
             extra["deferred_update"] = measure_deferred_update(tg, ctx)
         extra["model_sizes"] = measure_model_sizes(tg, ctx, shapes=MODEL_SHAPES[args.sizes])
+        extra["long_runs"] = measure_long_runs(tg, ctx)
         extra["argmax_flips"] = {"config2_512k": argmax_flips(ctx, rs, d_h, T),
                                  "config1_64k_skewed": flips_config1(tg, ctx, min(args.train_seconds, 10.0))}
 
@@ -880,7 +940,7 @@ def main():
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": "Mpkt/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if args.path == "fused_bf16" else "e4m3", "data": "synthetic",
         "config": {"workload": "512k rules x %s-packet trace (config-0 generator; half uniform-inside-rule, half Zipf 1.2)"
                    % ("16M" if n == N_PACKETS else str(n)),
                    "rules": N_RULES, "packets_per_step": n, "tuples": T, "network": "7-512-6x(512,512)-%d" % T,
