@@ -583,9 +583,13 @@ def cpu_model():
 def long_run_rules(n_plain, n_wild, seed):
     """n_plain rules of the config-0 generator plus n_wild rules with both prefixes wildcarded
     (one hash key of tuple (0,0): a run of n_wild+ rules) with exact ports and protocol that few
-    packets match, priorities interleaved at random: searches scan far into that run."""
+    packets match. The wildcard rules take priorities among the best quarter: a packet whose
+    answer lies below them compares it with every rule of the run."""
     rng = np.random.default_rng(seed)
     plain = wl.gen_rules(n_plain, seed)
+    both = (plain["sip_len"] == 0) & (plain["dip_len"] == 0)
+    plain["sip_len"][both] = 8                 # the (0,0) key holds the wildcard rules below only
+    plain["sip"][both] &= np.uint32(0xFF000000)
     wild = wl.gen_rules(n_wild, seed + 1)
     for f in ("sip", "dip"):
         wild[f] = 0
@@ -599,12 +603,13 @@ def long_run_rules(n_plain, n_wild, seed):
     rules = np.concatenate([plain, wild])
     rules["id"] = np.arange(len(rules))
     rules["priority"] = rng.permutation(len(rules))
+    rules["priority"][n_plain:] = rng.integers(0, len(rules) // 4, n_wild)
     return rules
 
 
-def measure_long_runs(tg, ctx, n_packets=1 << 22):
+def measure_long_runs(tg, ctx, n_packets=1 << 20):
     """512k rules plus 8,192 rules under tuple (0,0) (one run of more than 8k rules under one key),
-    4M packets: the search alone and the fused BF16 path, each with the warp-cooperative scan of
+    1M packets: the search alone and the fused BF16 path, each with the warp-cooperative scan of
     long runs and with one thread per run (TANG_SEARCH_SERIAL); ids against the oracle."""
     import torch
     from oracle import classify as oc

@@ -473,12 +473,16 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
                         const int col0 = unit * 64 + s * 32;
                         const uint32_t *a = s == 0 ? a0 : a1;
                         const float bl = s == 0 ? cc.b0 : cc.b1;
+                        // two columns per packed f32x2 instruction: v = acc + b (BF16), acc * d + b (FP8)
                         float v[32];
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) {
-                            const float b = __shfl_sync(0xFFFFFFFFu, bl, j);
-                            const float y = __uint_as_float(a[j]);
-                            v[j] = F8 ? fmaf(y, cc.d, b) : y + b;
+                        for (int j = 0; j < 16; ++j) {
+                            const float2 b = make_float2(__shfl_sync(0xFFFFFFFFu, bl, 2 * j),
+                                                         __shfl_sync(0xFFFFFFFFu, bl, 2 * j + 1));
+                            const float2 y = make_float2(__uint_as_float(a[2 * j]), __uint_as_float(a[2 * j + 1]));
+                            const float2 r = F8 ? fma_f2(y, make_float2(cc.d, cc.d), b) : add_f2(y, b);
+                            v[2 * j] = r.x;
+                            v[2 * j + 1] = r.y;
                         }
                         TC_TRACE(trace::kEpiX + (g * trace::kChunks + int(uses)) * 6 + 3 * s + 0, tr);
                         if (fc2) {
@@ -488,8 +492,11 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
                                 ptx::tmem_wait_ld();
 #pragma unroll
                                 for (int j = 0; j < 16; ++j) {
-                                    v[2 * j] += __uint_as_float(xr[j] << 16);
-                                    v[2 * j + 1] += __uint_as_float(xr[j] & 0xFFFF0000u);
+                                    const float2 r = add_f2(make_float2(v[2 * j], v[2 * j + 1]),
+                                                            make_float2(__uint_as_float(xr[j] << 16),
+                                                                        __uint_as_float(xr[j] & 0xFFFF0000u)));
+                                    v[2 * j] = r.x;
+                                    v[2 * j + 1] = r.y;
                                 }
                             } else {
                                 uint32_t xr[8];
@@ -498,10 +505,12 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
 #pragma unroll
                                 for (int j = 0; j < 8; ++j) {
                                     const float2 lo = e4m3x2_to_f2(xr[j]), hi = e4m3x2_to_f2(xr[j] >> 16);
-                                    v[4 * j + 0] = fmaf(lo.x, rr, v[4 * j + 0]);
-                                    v[4 * j + 1] = fmaf(lo.y, rr, v[4 * j + 1]);
-                                    v[4 * j + 2] = fmaf(hi.x, rr, v[4 * j + 2]);
-                                    v[4 * j + 3] = fmaf(hi.y, rr, v[4 * j + 3]);
+                                    const float2 r0 = fma_f2(lo, make_float2(rr, rr), make_float2(v[4 * j], v[4 * j + 1]));
+                                    const float2 r1 = fma_f2(hi, make_float2(rr, rr), make_float2(v[4 * j + 2], v[4 * j + 3]));
+                                    v[4 * j + 0] = r0.x;
+                                    v[4 * j + 1] = r0.y;
+                                    v[4 * j + 2] = r1.x;
+                                    v[4 * j + 3] = r1.y;
                                 }
                             }
                         }

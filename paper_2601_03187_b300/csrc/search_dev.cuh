@@ -71,11 +71,13 @@ struct Counters {
     uint32_t probes, rule_reads, slot_reads;
 };
 
-// Runs longer than this are scanned by the lanes of the warp together (scan_run_coop).
-constexpr uint32_t kCoopRun = 16;
+// A thread scans the first kCoopAfter rules of a run itself; if the scan has not ended there, the
+// rest of the run is scanned by the lanes of the warp together (scan_run_coop). Most scans end
+// within a few rules (at the first match or the first rule that cannot beat the current best).
+constexpr uint32_t kCoopAfter = 32;
 
-// Scan the runs of every lane of the calling group (the lanes that are executing this call
-// together) cooperatively: for each member's run in turn, the group reads consecutive rules of it
+// Scan the runs (or run remainders) of every lane of the calling group (the lanes that are
+// executing this call together) cooperatively: for each member's run in turn, the group reads consecutive rules of it
 // in one coalesced step per group size (lane of rank k takes rule base + k), and two ballots find
 // the first rule in run order that matches or that no longer beats the member's current best (the
 // run is priority-sorted, so the scan ends there). Each lane gets its own run's outcome: the
@@ -144,8 +146,8 @@ __device__ __forceinline__ bool probe_tuple(const Tables &tb, const TupleDesc &d
         c.slot_reads++;
         if (s.z == kEmpty) return false;
         if (s.x == ks && s.y == kd) {
-            if (coop && s.w > kCoopRun) return scan_run_coop(tb, s.z, s.w, t, h, best, c);
-            for (uint32_t j = 0; j < s.w; ++j) {
+            const uint32_t serial_len = coop && s.w > kCoopAfter ? kCoopAfter : s.w;
+            for (uint32_t j = 0; j < serial_len; ++j) {
                 if (!TANG_INDEX_OK(tb, s.z + j < tb.pool_size)) return false;
                 DRule r = load_rule(tb.rules + s.z + j);
                 c.rule_reads++;
@@ -155,6 +157,7 @@ __device__ __forceinline__ bool probe_tuple(const Tables &tb, const TupleDesc &d
                     return true;
                 }
             }
+            if (serial_len < s.w) return scan_run_coop(tb, s.z + serial_len, s.w - serial_len, t, h, best, c);
             return false;
         }
     }

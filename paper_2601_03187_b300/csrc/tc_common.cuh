@@ -55,6 +55,30 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
     return *reinterpret_cast<uint32_t *>(&v);
 }
+// Two FP32 operations in one instruction (the packed f32x2 forms of sm_100 and later): each
+// element is rounded to nearest even exactly as the scalar add / fma would round it.
+__device__ __forceinline__ uint64_t f2_pack(float lo, float hi) {
+    uint64_t d;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(lo), "f"(hi));
+    return d;
+}
+__device__ __forceinline__ float2 f2_unpack(uint64_t v) {
+    float2 r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+    return r;
+}
+__device__ __forceinline__ float2 add_f2(float2 a, float2 b) {
+    uint64_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2_pack(a.x, a.y)), "l"(f2_pack(b.x, b.y)));
+    return f2_unpack(d);
+}
+// a * b + c per element, one rounding each
+__device__ __forceinline__ float2 fma_f2(float2 a, float2 b, float2 c) {
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(f2_pack(a.x, a.y)), "l"(f2_pack(b.x, b.y)), "l"(f2_pack(c.x, c.y)));
+    return f2_unpack(d);
+}
+
 // ReLU, round to nearest even and pack two BF16: lo in bits 0-15, hi in bits 16-31.
 __device__ __forceinline__ uint32_t relu_bf16x2(float lo, float hi) {
     uint32_t d;

@@ -24,6 +24,47 @@ def load_rulesets(ctx, sizes, seed0=0):
     return out
 
 
+def test_config3_rulesets_every_request():
+    """The serving configuration at full size: four resident rulesets of 16k, 64k, 256k and 512k
+    rules, Poisson arrivals with batch sizes log-uniform in [1, 65536], paced submission while
+    others are in flight; every id of every request equals the oracle's."""
+    sizes = [16_384, 65_536, 262_144, 524_288]
+    with tg.Context(0) as ctx:
+        sets, pools = [], []
+        for k, n in enumerate(sizes):
+            rules = wl.gen_rules(n, 10 + k)
+            rs = ctx.load_ruleset(rules)
+            T = ctx.ruleset_info(rs)["n_tuples"]
+            ctx.load_model(rs, tg.pack_model(random_params(np.random.default_rng(k), C=T)))
+            sets.append((rs, rules))
+            pools.append(wl.gen_trace(rules, [("inside", 1 << 17), ("zipf", 1 << 17, 1.2)], 30 + k))
+        arrivals = wl.gen_serving_arrivals(400, len(sets), 2000.0, seed=5)
+        ctx.serve_start(max_inflight=8, max_batch=262_144, path="fused_bf16")
+        outs, handles, reqs = [], [], []
+        t0 = time.perf_counter()
+        for t_arr, which, size, seed in arrivals:
+            delay = t0 + t_arr - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            off = seed % (len(pools[which]) - size)
+            h = pools[which][off:off + size]
+            outs.append(np.full(size, 7, dtype=np.uint32))
+            reqs.append((which, h))
+            handles.append(ctx.serve_submit(sets[which][0], h, outs[-1]))
+        for r in handles:
+            assert ctx.serve_poll(r, wait_ms=60000) is not None
+        info = ctx.serve_info()
+        ctx.serve_stop()
+        assert info["packets"] == sum(len(h) for _, h in reqs)
+        for k in range(len(sets)):
+            idx = [i for i, (w, _) in enumerate(reqs) if w == k]
+            if not idx:
+                continue
+            got = np.concatenate([outs[i] for i in idx])
+            want = oc.classify(sets[k][1], np.concatenate([reqs[i][1] for i in idx]))
+            assert (got == want).all(), sizes[k]
+
+
 def test_requests_same_alone_and_in_the_mix():
     rng = np.random.default_rng(0)
     with tg.Context(0) as ctx:
