@@ -724,7 +724,7 @@ def main():
     ap.add_argument("--packets", type=int, default=N_PACKETS, help="use the first P packets of the trace")
     ap.add_argument("--path", default="fused_bf16", choices=["fused_bf16", "fused_fp8"],
                     help="the timed path of --quick runs (profiling one kernel); full runs time fused_bf16")
-    ap.add_argument("--variant", default=None, choices=[None, "n256"],
+    ap.add_argument("--variant", default=None, choices=[None, "n256", "pair"],
                     help="tensor-core kernel variant (default: the library's choice)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup

@@ -122,8 +122,10 @@ int tang::search_mode_of(uint32_t flags) {
     return ((flags & TANG_SEARCH_PAPER) ? 1 : 0) | ((flags & TANG_SEARCH_SERIAL) ? 2 : 0);
 }
 
-// Kernel variant requested by flag bits: 5 = the N=256 fused kernel, 0 = tuned or library default.
+// Kernel variant requested by flag bits: 5 = the N=256 fused kernel on one SM, 6 = on CTA pairs,
+// 0 = tuned or library default.
 static int variant_of(uint32_t flags) {
+    if (flags & TANG_FUSED_PAIR) return 6;
     if (flags & TANG_FUSED_N256) return 5;
     return 0;
 }

@@ -25,15 +25,17 @@
 // uniform broadcast per weight per warp, about 9k cycles per tile at one broadcast per cycle.
 //
 // Weight tiles are 256 rows x 128 bytes (32 KB), streamed by TMA through three stages (BF16) or
-// four (FP8, whose u buffer is half the size), so that at a chunk boundary the next chunk's first
+// four (FP8, whose u lives in TMEM), so that at a chunk boundary the next chunk's first
 // K-blocks are already in flight while the accumulator changes hands. The epilogue spends few
 // instructions per element: vector bias loads, ReLU folded into the packing conversion, and for
 // FP8 the output scale folded into the per-column constants (exact, the scales being powers of
 // two) and two-at-a-time E4M3 decoding of the residual. All waits are bounded (2 s of
 // %globaltimer) as in the other kernels.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <cstring>
 #include <vector>
 
 #include "search_dev.cuh"
@@ -44,7 +46,6 @@ namespace tang {
 
 namespace tc256 {
 constexpr int kM = 128;
-constexpr int kStageBytes = 32768;  // 256 rows x 128 bytes
 constexpr int kNumEpiWarps = 16;
 // Warp groups (4 warps each): 0 = producer (warp 0) and MMA issuer (warp 1); 1..4 = the epilogue;
 // 5 = the search. Every sub-partition gets one warp of each group.
@@ -58,19 +59,26 @@ static_assert(kRegCtl + 4 * kRegEpi + kRegSearch == 6 * kRegLaunch, "register sp
 static_assert(kThreads * kRegLaunch <= 65536, "register file");
 constexpr uint64_t kTimeoutNs = 2000000000ull;
 constexpr uint32_t kXCol = 256;
+// FP8 only: the FC1 output u (E4M3, 4 per 32-bit column: 128 columns at width 512) in the TMEM
+// columns BF16's wider x occupies, so that FC2 reads its A operand from TMEM as FC1 does (an
+// M=128, N=256 MMA measured 144 cycles with A in TMEM against 171 with A in shared memory)
+constexpr uint32_t kUCol = 384;
 constexpr int kL0K = 64;     // layer-0 contraction width (48 used, zero padded to one 128-byte row)
 constexpr int kL0Kused = 48;
 // Column group whose warps combine the partial argmax: its layer-0 units (3 and 7) are the last
 // ones the next tile's first MMAs need.
 constexpr int kArgG = 3;
 
-// Shared memory: u (the FC1 output as swizzled K-blocks of 128 rows x 128 bytes; its first 16 KB
-// also hold the next tile's layer-0 operand between the last FC2 and the next FC1 epilogue), the
-// weight stages, the predicted-tuple handoff to the search warps, the barriers, the partial argmax.
-template <bool F8, int HID>
+// Shared memory: for BF16 u (the FC1 output as swizzled K-blocks of 128 rows x 128 bytes; its
+// first 16 KB also hold the next tile's layer-0 operand between the last FC2 and the next FC1
+// epilogue), for FP8 (u in TMEM) the layer-0 operand alone; the weight stages, the predicted-tuple handoff to the search warps, the barriers, the partial argmax.
+// P: the CTA-pair kernel, whose CTAs each hold half of every 256-row weight tile (16 KB stages;
+// the freed shared memory buys deeper weight pipelines).
+template <bool F8, int HID, bool P = false>
 struct Layout {
-    static constexpr int kStages = F8 ? 4 : 3;
-    static constexpr int kYBytes = kM * HID * (F8 ? 1 : 2);
+    static constexpr int kStageBytes = P ? 16384 : 32768;  // 128 / 256 rows x 128 bytes
+    static constexpr int kStages = P ? (F8 ? 8 : 6) : (F8 ? 4 : 3);
+    static constexpr int kYBytes = F8 ? kM * 128 : kM * HID * 2;
     static constexpr int kOffStage = kYBytes;
     static constexpr int kOffTidx = kOffStage + kStages * kStageBytes;
     static constexpr int kOffBar = kOffTidx + 2 * kM * 4;
@@ -87,13 +95,23 @@ struct Layout {
 
 // 24 warps, launched at 80 registers per thread (6 x 32 x 80 = 15,360 of a sub-partition's 16K);
 // after setup the control group drops to 40, the search group to 56 and the epilogue rises to 96.
-template <bool F8, int HID>
+//
+// P (CTA pairs): the kernel runs in clusters of two CTAs on two SMs. Each CTA keeps its own
+// 128-packet tile, its own accumulator and x in its TMEM and its own u (BF16: shared memory, FP8: TMEM), but the
+// first CTA's MMA thread issues every MMA for both as one cta_group::2 MMA with M = 256: each CTA
+// loads only its 128 rows (output columns) of each weight tile, so an SM streams and reads half
+// the weight bytes per MMA and issues no MMAs of its own half the time. The barriers the MMAs wait
+// on (stages full, accumulator drained, activations published) live in the first CTA and count
+// both CTAs' arrivals; the MMA commits arrive in both CTAs.
+template <bool F8, int HID, bool P>
 __global__ void __launch_bounds__(tc256::kThreads, 1)
     k_tc256_classify(const __grid_constant__ CUtensorMap tm_hid, const __grid_constant__ CUtensorMap tm_out,
                      const __grid_constant__ CUtensorMap tm_l0, const TcParams p) {
     using namespace tc256;
-    using Lay = Layout<F8, HID>;
+    using Lay = Layout<F8, HID, P>;
     constexpr int kStages = Lay::kStages;
+    constexpr int kStageBytes = Lay::kStageBytes;
+    constexpr int kPair = P ? 2 : 1;  // CTAs that arrive on the MMA-side barriers
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t *sY = smem;
@@ -127,15 +145,15 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
             ptx::mbar_init(&empty[s], 1);
         }
         ptx::mbar_init(acc_full, 1);
-        ptx::mbar_init(acc_empty, kNumEpiWarps);
+        ptx::mbar_init(acc_empty, kPair * kNumEpiWarps);
         for (int b = 0; b < 2; ++b) {
             ptx::mbar_init(&tfull[b], 4);
             ptx::mbar_init(&tempty[b], kNumSearchWarps);
         }
-        for (int k = 0; k < 8; ++k) ptx::mbar_init(&act[k], kActArrivals);
+        for (int k = 0; k < 8; ++k) ptx::mbar_init(&act[k], kPair * kActArrivals);
         ptx::mbar_init(drain, 1);
         ptx::mbar_init(part_full, 4 * (kNumEpiWarps / 4 - 1));
-        ptx::mbar_init(feat_full, 4);
+        ptx::mbar_init(feat_full, kPair * 4);
         *sAbort = 0;
         ptx::fence_mbar_init();
     }
@@ -145,13 +163,40 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
         ptx::prefetch_tmap(&tm_l0);
     }
     if (warp == kWarpMma) {
-        ptx::tmem_alloc(sTmem, 512);
-        ptx::tmem_relinquish();
+        if (P) {
+            ptx::tmem_alloc_cg2(sTmem, 512);
+            ptx::tmem_relinquish_cg2();
+        } else {
+            ptx::tmem_alloc(sTmem, 512);
+            ptx::tmem_relinquish();
+        }
     }
     ptx::tc_fence_before();
-    __syncthreads();
+    if (P)
+        ptx::cluster_sync();  // both CTAs' barriers are initialised before any arrival from the other
+    else
+        __syncthreads();
     ptx::tc_fence_after();
     const uint32_t tmem = *sTmem;
+    // Tiles: a CTA pair takes pair-tiles pt = first, first + step, ...; its CTA of rank r works on
+    // tile 2 pt + r (past the last tile its rows are all beyond n: computed, never written).
+    const uint32_t rank = P ? ptx::cluster_ctarank() : 0u;
+    const uint32_t pt_first = P ? blockIdx.x >> 1 : blockIdx.x, pt_step = P ? gridDim.x >> 1 : gridDim.x;
+    const uint32_t n_pt = P ? (p.n_tiles + 1) >> 1 : p.n_tiles;
+    auto tile_of = [&](uint32_t pt) { return P ? 2 * pt + rank : pt; };
+    // shared::cluster address of a barrier in the first CTA of the pair (this CTA's own otherwise)
+    auto lead = [&](uint64_t *b) { return P ? ptx::mapa(ptx::smem_u32(b), 0) : ptx::smem_u32(b); };
+    // arrival on a barrier the MMA thread waits for
+    auto arrive_mma_side = [&](uint64_t *b) {
+        if (P)
+            ptx::mbar_arrive_cluster(lead(b));
+        else
+            ptx::mbar_arrive(b);
+    };
+    // waits on barriers that receive arrivals or MMA commits from the other CTA of a pair
+    auto wait_x = [&](uint64_t *b, uint32_t parity) {
+        return P ? ptx::mbar_wait_cl(b, parity, sAbort, kTimeoutNs) : ptx::mbar_wait(b, parity, sAbort, kTimeoutNs);
+    };
     auto fail = [&](int code) {
         atomicOr(p.err, code);
         *sAbort = 1;
@@ -166,7 +211,7 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
             uint32_t stage = 0, phase = 0, n_loads = 0;
             bool ok = true;
             auto next_stage = [&]() -> uint8_t * {
-                if (!ptx::mbar_wait(&empty[stage], phase ^ 1, sAbort, kTimeoutNs)) {
+                if (!wait_x(&empty[stage], phase ^ 1)) {
                     fail(1);
                     ok = false;
                     return nullptr;
@@ -181,13 +226,25 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
                     phase ^= 1;
                 }
             };
-            for (uint32_t tile = blockIdx.x; tile < p.n_tiles && ok; tile += gridDim.x) {
+            // one tile load: the whole box, or (pairs) a box of half its rows for each CTA, whose bytes
+            // the first CTA's barrier counts for both; the second CTA's half starts half the MMA's
+            // width `n` further (n < rows only in a narrower last output chunk, whose box is then
+            // partly unused; the output weights are padded, so it stays in bounds)
+            auto load = [&](uint8_t *dst, const CUtensorMap *m, int x, int y, uint32_t rows, uint32_t n) {
+                if (P) {
+                    if (rank == 0) ptx::mbar_arrive_expect_tx(&full[stage], rows * 128);
+                    ptx::tma_load_2d_cg2(dst, m, lead(&full[stage]), x, y + int(rank * n / 2));
+                } else {
+                    ptx::mbar_arrive_expect_tx(&full[stage], rows * 128);
+                    ptx::tma_load_2d(dst, m, &full[stage], x, y);
+                }
+            };
+            for (uint32_t pt = pt_first; pt < n_pt && ok; pt += pt_step) {
                 // layer 0: the 256-row chunks of the [HID][64] BF16 operand, one stage each
                 for (int c = 0; c < NCH && ok; ++c) {
                     uint8_t *dst = next_stage();
                     if (!dst) break;
-                    ptx::mbar_arrive_expect_tx(&full[stage], kStageBytes);
-                    ptx::tma_load_2d(dst, &tm_l0, &full[stage], 0, c * 256);
+                    load(dst, &tm_l0, 0, c * 256, 256, 256);
                     advance();
                 }
                 for (int L = 0; L <= nl && ok; ++L) {
@@ -196,48 +253,53 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
                         for (int kb = 0; kb < KB; ++kb) {
                             uint8_t *dst = next_stage();
                             if (!dst) break;
-                            if (L < nl) {
-                                ptx::mbar_arrive_expect_tx(&full[stage], kStageBytes);
-                                ptx::tma_load_2d(dst, &tm_hid, &full[stage], kb * KBW, L * HID + c * 256);
-                            } else {
-                                ptx::mbar_arrive_expect_tx(&full[stage], out_box * 128);
-                                ptx::tma_load_2d(dst, &tm_out, &full[stage], kb * KBW, c * 256);
-                            }
+                            if (L < nl)
+                                load(dst, &tm_hid, kb * KBW, L * HID + c * 256, 256, 256);
+                            else
+                                load(dst, &tm_out, kb * KBW, c * 256, out_box,
+                                     p.Cpad - 256u * c < 256u ? p.Cpad - 256u * c : 256u);
                             advance();
                         }
                 }
             }
-            // let the loads still in flight land before the CTA exits (bounded, abort ignored)
+            // let the loads still in flight land before the CTA exits (bounded, abort ignored); in a
+            // pair both CTAs' loads complete on the first CTA's barriers, and the second CTA stays
+            // until the first has seen them (the cluster barrier at the end)
             volatile int never = 0;
-            for (int s = 0; s < kStages; ++s) {
-                const uint32_t par = s < int(stage) ? phase : phase ^ 1;
-                ptx::mbar_wait(&full[s], par, &never, kTimeoutNs);
-            }
+            if (rank == 0)
+                for (int s = 0; s < kStages; ++s) {
+                    const uint32_t par = s < int(stage) ? phase : phase ^ 1;
+                    ptx::mbar_wait(&full[s], par, &never, kTimeoutNs);
+                }
         }
     } else if (warp == kWarpMma) {
-        // One thread issues every MMA. Plain loops over register state: this warp's issue rate
-        // bounds the tensor pipe's, so it keeps no state in captured lambdas or local memory.
-        if (lane == 0) {
-            const uint32_t idesc_h = ptx::idesc_make(128, 256, F8);
-            const uint32_t idesc_0 = ptx::idesc_make(128, 256, false);  // layer 0: BF16 on both paths
+        // One thread issues every MMA (in a pair, the first CTA's, for both). Plain loops over
+        // register state: this warp's issue rate bounds the tensor pipe's, so it keeps no state in
+        // captured lambdas or local memory.
+        if (lane == 0 && rank == 0) {
+            constexpr uint32_t kMmaM = P ? 256 : 128;
+            const uint32_t idesc_h = ptx::idesc_make(kMmaM, 256, F8);
+            const uint32_t idesc_0 = ptx::idesc_make(kMmaM, 256, false);  // layer 0: BF16 on both paths
+            // the second CTA's copy of a barrier (MMA commits arrive in both CTAs of a pair)
+            const uint32_t peer_off = P ? ptx::mapa(ptx::smem_u32(bars), 1) - ptx::smem_u32(bars) : 0u;
             const uint32_t y_addr = ptx::smem_u32(sY), st_addr = ptx::smem_u32(sStage);
             const uint64_t a0_desc = ptx::sdesc_sw128(y_addr);
             uint32_t stage = 0, phase = 0, uses = 0, lay = 0, ntile = 0;
             int err = 0;
-            for (uint32_t tile = blockIdx.x; tile < p.n_tiles && !err; tile += gridDim.x, ++ntile) {
+            for (uint32_t pt = pt_first; pt < n_pt && !err; pt += pt_step, ++ntile) {
                 // ---- layer 0: A = the header bytes (shared memory), B = the split weights
                 for (int c = 0; c < NCH; ++c, ++uses) {
                     TC_TRACE(trace::kMma + uses * 12 + 0, uses < uint32_t(trace::kChunks));
-                    if (uses > 0 && !ptx::mbar_wait(acc_empty, (uses - 1) & 1, sAbort, kTimeoutNs)) {
+                    if (uses > 0 && !wait_x(acc_empty, (uses - 1) & 1)) {
                         err = 2;
                         break;
                     }
                     TC_TRACE(trace::kMma + uses * 12 + 1, uses < uint32_t(trace::kChunks));
-                    if (c == 0 && !ptx::mbar_wait(feat_full, ntile & 1, sAbort, kTimeoutNs)) {
+                    if (c == 0 && !wait_x(feat_full, ntile & 1)) {
                         err = 512;
                         break;
                     }
-                    if (!ptx::mbar_wait(&full[stage], phase, sAbort, kTimeoutNs)) {
+                    if (!wait_x(&full[stage], phase)) {
                         err = 8;
                         break;
                     }
@@ -245,13 +307,28 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
                     ptx::tc_fence_after();
                     const uint64_t bd = ptx::sdesc_sw128(st_addr + stage * kStageBytes);
 #pragma unroll
-                    for (int kk = 0; kk < kL0Kused / 16; ++kk) ptx::mma_ss(tmem, a0_desc + 2 * kk, bd + 2 * kk, idesc_0, kk != 0, false);
-                    ptx::mma_commit(&empty[stage]);
+                    for (int kk = 0; kk < kL0Kused / 16; ++kk) {
+                        if (P)
+                            ptx::mma2_ss(tmem, a0_desc + 2 * kk, bd + 2 * kk, idesc_0, kk != 0, false);
+                        else
+                            ptx::mma_ss(tmem, a0_desc + 2 * kk, bd + 2 * kk, idesc_0, kk != 0, false);
+                    }
+                    if (P) {
+                        ptx::mma2_commit(ptx::smem_u32(&empty[stage]));
+                        ptx::mma2_commit(ptx::smem_u32(&empty[stage]) + peer_off);
+                    } else {
+                        ptx::mma_commit(&empty[stage]);
+                    }
                     if (++stage == kStages) {
                         stage = 0;
                         phase ^= 1;
                     }
-                    ptx::mma_commit(acc_full);
+                    if (P) {
+                        ptx::mma2_commit(ptx::smem_u32(acc_full));
+                        ptx::mma2_commit(ptx::smem_u32(acc_full) + peer_off);
+                    } else {
+                        ptx::mma_commit(acc_full);
+                    }
                     TC_TRACE(trace::kMma + uses * 12 + 10, uses < uint32_t(trace::kChunks));
                 }
                 for (int L = 0; L <= nl && !err; ++L, ++lay) {
@@ -259,20 +336,20 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
                     const int nch = L == nl ? n_oc : NCH;
                     for (int c = 0; c < nch && !err; ++c, ++uses) {
                         const uint32_t idesc =
-                            L == nl ? ptx::idesc_make(128, p.Cpad - 256u * c < 256u ? p.Cpad - 256u * c : 256u, F8) : idesc_h;
+                            L == nl ? ptx::idesc_make(kMmaM, p.Cpad - 256u * c < 256u ? p.Cpad - 256u * c : 256u, F8) : idesc_h;
                         TC_TRACE(trace::kMma + uses * 12 + 0, uses < uint32_t(trace::kChunks));
-                        if (!ptx::mbar_wait(acc_empty, (uses - 1) & 1, sAbort, kTimeoutNs)) {
+                        if (!wait_x(acc_empty, (uses - 1) & 1)) {
                             err = 2;
                             break;
                         }
                         TC_TRACE(trace::kMma + uses * 12 + 1, uses < uint32_t(trace::kChunks));
                         ptx::tc_fence_after();
                         for (int kb = 0; kb < KB; ++kb) {
-                            if (c == 0 && !ptx::mbar_wait(&act[kb], lay & 1, sAbort, kTimeoutNs)) {
+                            if (c == 0 && !wait_x(&act[kb], lay & 1)) {
                                 err = 4;
                                 break;
                             }
-                            if (!ptx::mbar_wait(&full[stage], phase, sAbort, kTimeoutNs)) {
+                            if (!wait_x(&full[stage], phase)) {
                                 err = 8;
                                 break;
                             }
@@ -282,27 +359,59 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
                             if (a_tmem) {
                                 const uint32_t ta = tmem + kXCol + kb * 32;
 #pragma unroll
-                                for (int kk = 0; kk < 4; ++kk) ptx::mma_ts(tmem, ta + kk * 8, bd + 2 * kk, idesc, (kb | kk) != 0, F8);
-                            } else {
+                                for (int kk = 0; kk < 4; ++kk) {
+                                    if (P)
+                                        ptx::mma2_ts(tmem, ta + kk * 8, bd + 2 * kk, idesc, (kb | kk) != 0, F8);
+                                    else
+                                        ptx::mma_ts(tmem, ta + kk * 8, bd + 2 * kk, idesc, (kb | kk) != 0, F8);
+                                }
+                            } else if (F8) {  // FC2, FP8: A = u from TMEM
+                                const uint32_t ta = tmem + kUCol + kb * 32;
+#pragma unroll
+                                for (int kk = 0; kk < 4; ++kk) {
+                                    if (P)
+                                        ptx::mma2_ts(tmem, ta + kk * 8, bd + 2 * kk, idesc, (kb | kk) != 0, F8);
+                                    else
+                                        ptx::mma_ts(tmem, ta + kk * 8, bd + 2 * kk, idesc, (kb | kk) != 0, F8);
+                                }
+                            } else {  // FC2, BF16: A = u from shared memory
                                 const uint64_t ad = a0_desc + uint64_t(kb) * (16384 >> 4);
 #pragma unroll
-                                for (int kk = 0; kk < 4; ++kk) ptx::mma_ss(tmem, ad + 2 * kk, bd + 2 * kk, idesc, (kb | kk) != 0, F8);
+                                for (int kk = 0; kk < 4; ++kk) {
+                                    if (P)
+                                        ptx::mma2_ss(tmem, ad + 2 * kk, bd + 2 * kk, idesc, (kb | kk) != 0, F8);
+                                    else
+                                        ptx::mma_ss(tmem, ad + 2 * kk, bd + 2 * kk, idesc, (kb | kk) != 0, F8);
+                                }
                             }
-                            ptx::mma_commit(&empty[stage]);
+                            if (P) {
+                                ptx::mma2_commit(ptx::smem_u32(&empty[stage]));
+                                ptx::mma2_commit(ptx::smem_u32(&empty[stage]) + peer_off);
+                            } else {
+                                ptx::mma_commit(&empty[stage]);
+                            }
                             if (++stage == kStages) {
                                 stage = 0;
                                 phase ^= 1;
                             }
                         }
                         if (err) break;
-                        ptx::mma_commit(acc_full);
+                        if (P) {
+                            ptx::mma2_commit(ptx::smem_u32(acc_full));
+                            ptx::mma2_commit(ptx::smem_u32(acc_full) + peer_off);
+                        } else {
+                            ptx::mma_commit(acc_full);
+                        }
                         TC_TRACE(trace::kMma + uses * 12 + 10, uses < uint32_t(trace::kChunks));
                     }
                 }
             }
             if (err) fail(err);
             volatile int never = 0;
-            ptx::mma_commit(drain);
+            if (P)
+                ptx::mma2_commit(ptx::smem_u32(drain));
+            else
+                ptx::mma_commit(drain);
             ptx::mbar_wait(drain, 0, &never, kTimeoutNs);
         }
     }  // warps 2 and 3 of the control group have no role
@@ -317,28 +426,21 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
         const float *sa = p.sa;
         uint32_t uses = 0, tcnt = 0;
         bool ok = true;
+        // BF16 u: 16 values of row r into the swizzled K-major shared-memory tile FC2 reads
         auto store_smem = [&](const uint32_t *w, int col0) {
-            if (!F8) {
-                const int kb = col0 >> 6, j0 = (col0 & 63) >> 3;
-                uint8_t *row = sY + kb * 16384 + r * 128;
+            const int kb = col0 >> 6, j0 = (col0 & 63) >> 3;
+            uint8_t *row = sY + kb * 16384 + r * 128;
 #pragma unroll
-                for (int k = 0; k < 4; ++k)
-                    *reinterpret_cast<uint4 *>(row + (((j0 + k) ^ (r & 7)) << 4)) =
-                        make_uint4(w[4 * k], w[4 * k + 1], w[4 * k + 2], w[4 * k + 3]);
-            } else {
-                const int kb = col0 >> 7, j0 = (col0 & 127) >> 4;
-                uint8_t *row = sY + kb * 16384 + r * 128;
-#pragma unroll
-                for (int k = 0; k < 2; ++k)
-                    *reinterpret_cast<uint4 *>(row + (((j0 + k) ^ (r & 7)) << 4)) =
-                        make_uint4(w[4 * k], w[4 * k + 1], w[4 * k + 2], w[4 * k + 3]);
-            }
+            for (int k = 0; k < 4; ++k)
+                *reinterpret_cast<uint4 *>(row + (((j0 + k) ^ (r & 7)) << 4)) =
+                    make_uint4(w[4 * k], w[4 * k + 1], w[4 * k + 2], w[4 * k + 3]);
         };
         auto x_col = [&](int col0) -> uint32_t { return tmem + lane_base + kXCol + (F8 ? col0 / 4 : col0 / 2); };
+        [[maybe_unused]] auto u_col = [&](int col0) -> uint32_t { return tmem + lane_base + kUCol + col0 / 4; };
         auto act_arrive = [&](int col0) {
             ptx::tc_fence_before();
             __syncwarp();
-            if (lane == 0) ptx::mbar_arrive(&act[col0 / KBW]);
+            if (lane == 0) arrive_mma_side(&act[col0 / KBW]);
         };
         // ReLU, round and store 32 activations (columns col0 ..) of the next layer's input; for FP8
         // the values are already in the next layer's scaled units
@@ -356,10 +458,7 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
 #pragma unroll
                 for (int j = 0; j < 8; ++j)
                     w[j] = relu_e4m3x2(v[4 * j], v[4 * j + 1]) | (relu_e4m3x2(v[4 * j + 2], v[4 * j + 3]) << 16);
-                if (to_x)
-                    ptx::tmem_st8(x_col(col0), w);
-                else
-                    store_smem(w, col0);
+                ptx::tmem_st8(to_x ? x_col(col0) : u_col(col0), w);
             }
         };
         // Layer-0 operand of tile t, row r (the g == 0 warps): the header bytes as BF16 in the
@@ -393,7 +492,7 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
                 *reinterpret_cast<uint4 *>(row + ((j ^ (r & 7)) << 4)) = make_uint4(w[4 * j], w[4 * j + 1], w[4 * j + 2], w[4 * j + 3]);
             ptx::fence_proxy_async_smem();
             __syncwarp();
-            if (lane == 0) ptx::mbar_arrive(feat_full);
+            if (lane == 0) arrive_mma_side(feat_full);
         };
 
         // Per-column constants of the hidden layers, one per lane: the bias (FP8: b * s_out) of
@@ -413,12 +512,12 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
             return ColConst{__ldg(bv + col), __ldg(bv + col + 32), F8 ? __ldg(p.fold8 + size_t(L) * HID) : 0.f};
         };
         ColConst next_cc = load_cc(0, 0);
-        if (g == 0) write_features(blockIdx.x);
-        for (uint32_t tile = blockIdx.x; tile < p.n_tiles && ok; tile += gridDim.x) {
-            const uint32_t i = tile * kM + r;
+        if (g == 0 && pt_first < n_pt) write_features(tile_of(pt_first));
+        for (uint32_t pt = pt_first; pt < n_pt && ok; pt += pt_step) {
+            const uint32_t i = tile_of(pt) * kM + r;
             // ---- layer 0 from the accumulator (bias included): units 4c+g of x
             for (int c = 0; c < NCH; ++c, ++uses) {
-                if (!ptx::mbar_wait(acc_full, uses & 1, sAbort, kTimeoutNs)) {
+                if (!wait_x(acc_full, uses & 1)) {
                     fail(16);
                     ok = false;
                     break;
@@ -431,7 +530,7 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
                 ptx::tmem_wait_ld();
                 ptx::tc_fence_before();
                 __syncwarp();
-                if (lane == 0) ptx::mbar_arrive(acc_empty);
+                if (lane == 0) arrive_mma_side(acc_empty);
                 emit(reinterpret_cast<const float *>(a0), unit * 64, true);
                 emit(reinterpret_cast<const float *>(a1), unit * 64 + 32, true);
                 ptx::tmem_wait_st();
@@ -452,7 +551,7 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
                     // this chunk's column constants, loaded one chunk ago; now the next chunk's
                     const ColConst cc = next_cc;
                     next_cc = c + 1 < NCH ? load_cc(L, c + 1) : load_cc(L + 1 < nl ? L + 1 : 0, 0);
-                    if (!ptx::mbar_wait(acc_full, uses & 1, sAbort, kTimeoutNs)) {
+                    if (!wait_x(acc_full, uses & 1)) {
                         fail(16);
                         ok = false;
                         break;
@@ -466,7 +565,7 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
                     // the accumulator may take the next chunk's MMAs now
                     ptx::tc_fence_before();
                     __syncwarp();
-                    if (lane == 0) ptx::mbar_arrive(acc_empty);
+                    if (lane == 0) arrive_mma_side(acc_empty);
                     TC_TRACE(tslot + 2, tr);
 #pragma unroll
                     for (int s = 0; s < 2; ++s) {
@@ -518,7 +617,7 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
                         emit(v, col0, fc2);
                         TC_TRACE(trace::kEpiX + (g * trace::kChunks + int(uses)) * 6 + 3 * s + 2, tr);
                     }
-                    if (fc2)
+                    if (fc2 || F8)
                         ptx::tmem_wait_st();
                     else
                         ptx::fence_proxy_async_smem();
@@ -526,7 +625,7 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
                     TC_TRACE(tslot + 3, tr);
                     // after the last FC2 chunk (its MMAs, the last readers of u, have completed):
                     // the next tile's layer-0 operand
-                    if (L == nl - 1 && c == NCH - 1 && g == 0 && tile + gridDim.x < p.n_tiles) write_features(tile + gridDim.x);
+                    if (L == nl - 1 && c == NCH - 1 && g == 0 && pt + pt_step < n_pt) write_features(tile_of(pt + pt_step));
                 }
             }
             if (!ok) break;
@@ -539,7 +638,7 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
                 const float *bias = p.bias + nl * HID;
                 const float *dq = F8 ? p.dq + nl * HID : nullptr;
                 for (int oc = 0; oc < n_oc; ++oc) {
-                    if (!ptx::mbar_wait(acc_full, uses & 1, sAbort, kTimeoutNs)) {
+                    if (!wait_x(acc_full, uses & 1)) {
                         fail(32);
                         ok = false;
                         break;
@@ -567,7 +666,7 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
                     }
                     ptx::tc_fence_before();
                     __syncwarp();
-                    if (lane == 0) ptx::mbar_arrive(acc_empty);
+                    if (lane == 0) arrive_mma_side(acc_empty);
                 }
                 if (!ok) break;
                 const uint32_t t = tcnt & 1, tu = tcnt >> 1;  // this CTA's tile count: barrier parities
@@ -619,7 +718,7 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
             uint32_t tcnt = 0;
             uint32_t st_pk = 0, st_match = 0, st_correct = 0, st_hit = 0, st_fb = 0;
             Counters cn{0, 0, 0};
-            for (uint32_t tile = blockIdx.x; tile < p.n_tiles; tile += gridDim.x) {
+            for (uint32_t pt = pt_first; pt < n_pt; pt += pt_step) {
                 const uint32_t t = tcnt & 1, tu = tcnt >> 1;
                 ++tcnt;
                 if (!ptx::mbar_wait(&tfull[t], tu & 1, sAbort, kTimeoutNs)) {
@@ -632,7 +731,7 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
                 const int pred = sTidx[t * kM + r];
                 __syncwarp();
                 if (lane == 0) ptx::mbar_arrive(&tempty[t]);
-                const uint32_t i = tile * kM + r;
+                const uint32_t i = tile_of(pt) * kM + r;
                 if (i < p.n) {
                     // headers and ids stream through L2 with evict-first hints, the tables stay
                     const Hdr h = load_header_stream(p.headers + i);
@@ -668,9 +767,17 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
     }
 
     ptx::tc_fence_before();
-    __syncthreads();
+    if (P)
+        ptx::cluster_sync();  // the first CTA's MMAs into this CTA's TMEM and its loads have completed
+    else
+        __syncthreads();
     ptx::tc_fence_after();
-    if (warp == kWarpMma) ptx::tmem_dealloc(tmem, 512);
+    if (warp == kWarpMma) {
+        if (P)
+            ptx::tmem_dealloc_cg2(tmem, 512);
+        else
+            ptx::tmem_dealloc(tmem, 512);
+    }
 }
 
 namespace {
@@ -713,7 +820,9 @@ void layer0_operand(const float *W0, const float *b0, uint32_t N, float s, __nv_
 // with their maps, for width N = 256 or 512.
 int tc256_prepare_model(tang_ctx *ctx, DeviceModel &m) {
     if (!m.d_wbf16 || (m.N != 256 && m.N != 512)) return TANG_OK;
-    Tc256Maps *maps = static_cast<Tc256Maps *>(aligned_alloc(64, 2 * sizeof(Tc256Maps)));
+    // [BF16, FP8] with whole 256-row boxes, then [BF16, FP8] with half boxes for the CTA pairs
+    Tc256Maps *maps = static_cast<Tc256Maps *>(aligned_alloc(64, 4 * sizeof(Tc256Maps)));
+    std::memset(static_cast<void *>(maps), 0, 4 * sizeof(Tc256Maps));
     m.tmap256 = maps;
     const uint32_t N = m.N;
     const float *W0 = m.host_params.data(), *b0 = W0 + size_t(7) * N;
@@ -726,46 +835,91 @@ int tc256_prepare_model(tang_ctx *ctx, DeviceModel &m) {
     // output tiles of min(Cpad, 256) rows; past 256 the copies hold whole 256-row tiles
     const size_t hid = size_t(m.layers) * m.N * m.N;
     const uint32_t out_rows = m.Cpad <= 256 ? m.Cpad : (m.Cpad + 255) / 256 * 256, out_box = std::min<uint32_t>(m.Cpad, 256);
-    if ((rc = make_tmap(ctx, &maps[0].out, static_cast<__nv_bfloat16 *>(m.d_wbf16) + hid, out_rows, false, out_box, N)))
-        return rc;
-    if ((rc = make_tmap(ctx, &maps[0].hid, m.d_wbf16, m.layers * N, false, 256, N))) return rc;
-    if ((rc = make_tmap(ctx, &maps[0].l0, m.d_l0, N, false, 256, tc256::kL0K))) return rc;
-    if (m.d_wfp8) {
-        if ((rc = make_tmap(ctx, &maps[1].out, static_cast<uint8_t *>(m.d_wfp8) + hid, out_rows, true, out_box, N)))
+    for (uint32_t half = 1; half <= 2; ++half) {  // box rows / half: 1 = whole tiles, 2 = pair halves
+        Tc256Maps *mp = maps + (half - 1) * 2;
+        if ((rc = make_tmap(ctx, &mp[0].out, static_cast<__nv_bfloat16 *>(m.d_wbf16) + hid, out_rows, false,
+                            out_box / half, N)))
             return rc;
-        if ((rc = make_tmap(ctx, &maps[1].hid, m.d_wfp8, m.layers * N, true, 256, N))) return rc;
-        rc = make_tmap(ctx, &maps[1].l0, static_cast<__nv_bfloat16 *>(m.d_l0) + size_t(N) * tc256::kL0K, N, false, 256,
-                       tc256::kL0K);
+        if ((rc = make_tmap(ctx, &mp[0].hid, m.d_wbf16, m.layers * N, false, 256 / half, N))) return rc;
+        if ((rc = make_tmap(ctx, &mp[0].l0, m.d_l0, N, false, 256 / half, tc256::kL0K))) return rc;
+        if (m.d_wfp8) {
+            if ((rc = make_tmap(ctx, &mp[1].out, static_cast<uint8_t *>(m.d_wfp8) + hid, out_rows, true, out_box / half,
+                                N)))
+                return rc;
+            if ((rc = make_tmap(ctx, &mp[1].hid, m.d_wfp8, m.layers * N, true, 256 / half, N))) return rc;
+            if ((rc = make_tmap(ctx, &mp[1].l0, static_cast<__nv_bfloat16 *>(m.d_l0) + size_t(N) * tc256::kL0K, N, false,
+                                256 / half, tc256::kL0K)))
+                return rc;
+        }
     }
     return rc;
 }
 
-template <bool F8, int HID>
+// Pair launches (P) run in clusters of two CTAs: grid = 2 x the pairs that fit at once (one CTA
+// per SM), capped by the tuned grid and by the pair-tiles.
+template <bool F8, int HID, bool P>
 static int tc256_launch_t(tang_ctx *ctx, const Tc256Maps &maps, const TcParams &prm, cudaStream_t st, uint32_t grid) {
-    constexpr int kSmem = tc256::Layout<F8, HID>::kSmemBytes;
+    constexpr int kSmem = tc256::Layout<F8, HID, P>::kSmemBytes;
     static bool attr_done = false;
+    static uint32_t max_pairs = 0;
     if (!attr_done) {
         // the setmaxnreg split assumes the launch register count it was sized for: with any other
         // count an increase could wait forever, so refuse to launch
         cudaFuncAttributes fa{};
-        cudaError_t e = cudaFuncGetAttributes(&fa, k_tc256_classify<F8, HID>);
+        cudaError_t e = cudaFuncGetAttributes(&fa, k_tc256_classify<F8, HID, P>);
         if (e != cudaSuccess) return set_err(ctx, TANG_EDEVICE, "N=256 kernel attributes: %s", cudaGetErrorString(e));
         if (fa.numRegs != tc256::kRegLaunch)
             return set_err(ctx, TANG_EDEVICE, "N=256 kernel built with %d registers per thread, expected %d", fa.numRegs,
                            tc256::kRegLaunch);
-        e = cudaFuncSetAttribute(k_tc256_classify<F8, HID>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+        e = cudaFuncSetAttribute(k_tc256_classify<F8, HID, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
         if (e != cudaSuccess) return set_err(ctx, TANG_EDEVICE, "smem attribute (N=256): %s", cudaGetErrorString(e));
+        if (P) {
+            max_pairs = uint32_t(ctx->sm_count / 2);
+            cudaLaunchConfig_t q = {};
+            q.gridDim = dim3(2 * max_pairs, 1, 1);
+            q.blockDim = dim3(tc256::kThreads, 1, 1);
+            q.dynamicSmemBytes = kSmem;
+            cudaLaunchAttribute qa[1];
+            qa[0].id = cudaLaunchAttributeClusterDimension;
+            qa[0].val.clusterDim.x = 2;
+            qa[0].val.clusterDim.y = 1;
+            qa[0].val.clusterDim.z = 1;
+            q.attrs = qa;
+            q.numAttrs = 1;
+            int c = 0;
+            if (cudaOccupancyMaxActiveClusters(&c, k_tc256_classify<F8, HID, P>, &q) == cudaSuccess && c > 0)
+                max_pairs = std::min<uint32_t>(max_pairs, uint32_t(c));
+            cudaGetLastError();
+            if (max_pairs == 0) return set_err(ctx, TANG_EUNSUPPORTED, "no CTA pair fits on this device");
+        }
         attr_done = true;
     }
-    k_tc256_classify<F8, HID><<<grid, tc256::kThreads, kSmem, st>>>(maps.hid, maps.out, maps.l0, prm);
+    if (!P) {
+        k_tc256_classify<F8, HID, P><<<grid, tc256::kThreads, kSmem, st>>>(maps.hid, maps.out, maps.l0, prm);
+    } else {
+        const uint32_t pairs = std::max<uint32_t>(1, std::min<uint32_t>({max_pairs, (prm.n_tiles + 1) / 2, (grid + 1) / 2}));
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(2 * pairs, 1, 1);
+        cfg.blockDim = dim3(tc256::kThreads, 1, 1);
+        cfg.dynamicSmemBytes = kSmem;
+        cfg.stream = st;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 2;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        cudaLaunchKernelEx(&cfg, k_tc256_classify<F8, HID, P>, maps.hid, maps.out, maps.l0, prm);
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return set_err(ctx, TANG_EDEVICE, "N=256 kernel launch: %s", cudaGetErrorString(e));
     return TANG_OK;
 }
 
-int tc256_launch(tang_ctx *ctx, DeviceModel &m, const TcParams &prm, bool f8, cudaStream_t st, int grid_cap) {
+int tc256_launch(tang_ctx *ctx, DeviceModel &m, const TcParams &prm, bool f8, cudaStream_t st, int grid_cap, bool pair) {
     if (!m.tmap256 || !m.d_l0 || (f8 && (!m.d_wfp8 || !m.d_fold8))) return TANG_EUNSUPPORTED;
-    const Tc256Maps &maps = static_cast<const Tc256Maps *>(m.tmap256)[f8 ? 1 : 0];
+    const Tc256Maps &maps = static_cast<const Tc256Maps *>(m.tmap256)[(pair ? 2 : 0) + (f8 ? 1 : 0)];
     uint32_t grid = uint32_t(grid_cap > 0 ? grid_cap : ctx->sm_count);
     grid = std::min<uint32_t>(prm.n_tiles, std::min<uint32_t>(grid, uint32_t(ctx->sm_count)));
     TcParams prm_t = prm;
@@ -775,10 +929,17 @@ int tc256_launch(tang_ctx *ctx, DeviceModel &m, const TcParams &prm, bool f8, cu
     cudaMemsetAsync(d_trace, 0, sizeof(unsigned long long) * trace::kTotal, st);
     prm_t.trace = d_trace;
 #endif
-    const int rc = m.N == 512 ? (f8 ? tc256_launch_t<true, 512>(ctx, maps, prm_t, st, grid)
-                                    : tc256_launch_t<false, 512>(ctx, maps, prm_t, st, grid))
-                              : (f8 ? tc256_launch_t<true, 256>(ctx, maps, prm_t, st, grid)
-                                    : tc256_launch_t<false, 256>(ctx, maps, prm_t, st, grid));
+    int rc;
+    if (pair)
+        rc = m.N == 512 ? (f8 ? tc256_launch_t<true, 512, true>(ctx, maps, prm_t, st, grid)
+                              : tc256_launch_t<false, 512, true>(ctx, maps, prm_t, st, grid))
+                        : (f8 ? tc256_launch_t<true, 256, true>(ctx, maps, prm_t, st, grid)
+                              : tc256_launch_t<false, 256, true>(ctx, maps, prm_t, st, grid));
+    else
+        rc = m.N == 512 ? (f8 ? tc256_launch_t<true, 512, false>(ctx, maps, prm_t, st, grid)
+                              : tc256_launch_t<false, 512, false>(ctx, maps, prm_t, st, grid))
+                        : (f8 ? tc256_launch_t<true, 256, false>(ctx, maps, prm_t, st, grid)
+                              : tc256_launch_t<false, 256, false>(ctx, maps, prm_t, st, grid));
     if (rc) return rc;
 #ifdef TANG_TC_TRACE
     if (const char *path = getenv("TANG_TC_TRACE_FILE")) {

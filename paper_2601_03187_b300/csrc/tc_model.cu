@@ -150,15 +150,15 @@ int tc_prepare_model(tang_ctx *ctx, DeviceModel &m) {
     return TANG_OK;
 }
 
-int tc256_launch(tang_ctx *ctx, DeviceModel &m, const TcParams &prm, bool f8, cudaStream_t st, int grid_cap);
+int tc256_launch(tang_ctx *ctx, DeviceModel &m, const TcParams &prm, bool f8, cudaStream_t st, int grid_cap, bool pair);
 
 int tc_launch(tang_ctx *ctx, Ruleset &rs, const tang_header *h, uint32_t n, uint32_t *ids, float *logits,
               int32_t *tuple, int precision, bool fused_search, DevStats *stats, cudaStream_t st,
               const TuneEntry *tune, int variant, int mode) {
     if (n == 0) return TANG_OK;
-    // variant 0 = the tuned choice, else the library default; TANG_VARIANT_N256 (5) is the only kernel
+    // variant 0 = the tuned choice, else the library default: 5 = one CTA per SM, 6 = CTA pairs
     const int v = variant ? variant : (tune && tune->fused_variant ? tune->fused_variant : 5);
-    if (v != 5) return set_err(ctx, TANG_EINVAL, "unknown tensor-core kernel variant %d", v);
+    if (v != 5 && v != 6) return set_err(ctx, TANG_EINVAL, "unknown tensor-core kernel variant %d", v);
     DeviceModel &m = *rs.model;
     const bool f8 = precision == TANG_FP8;
     if (!m.d_wbf16 || (f8 && !m.d_wfp8)) return set_err(ctx, TANG_EUNSUPPORTED, "no tensor-core copy of this model");
@@ -181,7 +181,7 @@ int tc_launch(tang_ctx *ctx, Ruleset &rs, const tang_header *h, uint32_t n, uint
     prm.Cpad = m.Cpad;
     prm.fused_search = fused_search && ids ? 1 | (mode << 1) : 0;
     prm.trace = nullptr;
-    const int rc = tc256_launch(ctx, m, prm, f8, st, tune ? tune->fused_grid : 0);
+    const int rc = tc256_launch(ctx, m, prm, f8, st, tune ? tune->fused_grid : 0, v == 6);
     if (rc == TANG_EUNSUPPORTED)
         return set_err(ctx, TANG_EUNSUPPORTED, "no tensor-core kernel for a %u-block, %u-class model", m.blocks, m.C);
     return rc;

@@ -1,8 +1,8 @@
 // Launch-shape autotuner: times the candidate launch shapes of a path on a caller-supplied
 // device batch and keeps the fastest per (ruleset, path). Candidates:
 //   search kernel (no-network, staged and plain paths): threads per block x blocks per SM;
-//   fused kernel: the number of persistent CTAs (one per SM, or a divisor-friendly subset so
-//   that the tile count spreads evenly).
+//   fused kernel: one CTA per SM or CTA pairs, and the number of persistent CTAs (one per SM, or a
+//   divisor-friendly subset so that the tile count spreads evenly).
 #include <algorithm>
 
 #include "internal.h"
@@ -36,12 +36,13 @@ extern "C" int tang_autotune(tang_ctx *ctx, uint32_t rsh, const tang_header *d_h
                 grids.push_back(g);
                 break;
             }
-        for (int g : grids) {
-            TuneEntry e;
-            e.fused_variant = 5;
-            e.fused_grid = g;
-            cands.push_back(e);
-        }
+        for (int v : {5, 6})
+            for (int g : grids) {
+                TuneEntry e;
+                e.fused_variant = v;
+                e.fused_grid = g;
+                cands.push_back(e);
+            }
     } else {
         for (int th : {128, 256, 512})
             for (int bps : {2, 4, 8, 16}) {
@@ -97,7 +98,7 @@ extern "C" int tang_autotune_set(tang_ctx *ctx, uint32_t rsh, uint32_t path, int
     if (!ctx) return TANG_EINVAL;
     auto it = ctx->rulesets.find(rsh);
     if (it == ctx->rulesets.end()) return set_err(ctx, TANG_ENOTFOUND, "unknown ruleset %u", rsh);
-    if ((variant != 0 && variant != 5) || grid < 0 || grid > ctx->sm_count)
+    if ((variant != 0 && variant != 5 && variant != 6) || grid < 0 || grid > ctx->sm_count)
         return set_err(ctx, TANG_EINVAL, "variant %d / grid %d out of range", variant, grid);
     const bool th_ok = search_threads == 0 || search_threads == 128 || search_threads == 256 || search_threads == 512;
     if (!th_ok || search_bps < 0 || search_bps > 16 || search_threads * search_bps > 2048)

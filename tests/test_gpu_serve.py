@@ -194,7 +194,7 @@ def test_autotune_keeps_ids_exact():
             choice = ctx.autotune_get(rs, path)
             assert choice["ms"] > 0
             if path == "fused_bf16":
-                assert choice["variant"] == "n256"
+                assert choice["variant"] in ("n256", "pair")
             else:
                 assert choice["search_threads"] in (128, 256, 512) and choice["search_bps"] in (2, 4, 8, 16)
             ids = ids_dev(len(h))

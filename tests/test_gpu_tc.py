@@ -30,11 +30,15 @@ def lowp(prec, p, X, amax):
     return mlp_lowp.forward_bf16(p, X) if prec == "bf16" else mlp_lowp.forward_fp8(p, X, amax)
 
 
-def infer(ctx, rs, h, C, precision):
+# the fused kernel on one SM per tile, and on CTA pairs (cta_group::2)
+VARIANTS = ["n256", "pair"]
+
+
+def infer(ctx, rs, h, C, precision, variant=None):
     d = to_dev(h)
     z = torch.zeros((len(h), C), dtype=torch.float32, device="cuda")
     t = torch.zeros(len(h), dtype=torch.int32, device="cuda")
-    ctx.infer(rs, d, z, t, precision=precision)
+    ctx.infer(rs, d, z, t, precision=precision, variant=variant)
     torch.cuda.synchronize()
     return z.cpu().numpy(), t.cpu().numpy()
 
@@ -58,12 +62,13 @@ def setup():
     ctx.close()
 
 
+@pytest.mark.parametrize("variant", VARIANTS)
 @pytest.mark.parametrize("prec", ["bf16", "fp8"])
-def test_logits_match_the_oracle_element_by_element(setup, prec):
+def test_logits_match_the_oracle_element_by_element(setup, prec, variant):
     ctx, rules, rs, T, p, amax, h = setup
     hs = h[:4096 + 37]                      # 32 full tiles and a ragged one
     X = mlp.features(hs)
-    z, tup = infer(ctx, rs, hs, T, PREC[prec])
+    z, tup = infer(ctx, rs, hs, T, PREC[prec], variant)
     z_or, mag = lowp(prec, p, X, amax)
     stats, ok = compare_logits(z, z_or, mag, K=512, rho=RHO[prec])
     print(prec, stats)
@@ -117,9 +122,10 @@ EXACT_CASES = [("cfg0", 512, 6), ("cfg0", 512, 1), ("cfg0", 256, 6), ("cfg0", 25
                (200, 512, 2), (350, 512, 2), (1500, 512, 1), (350, 256, 2)]
 
 
+@pytest.mark.parametrize("variant", VARIANTS)
 @pytest.mark.parametrize("case", EXACT_CASES, ids=[f"{r}-{w}x{b}" for r, w, b in EXACT_CASES])
 @pytest.mark.parametrize("prec", ["bf16", "fp8"])
-def test_exact_networks_bit_for_bit(prec, case):
+def test_exact_networks_bit_for_bit(prec, case, variant):
     """On networks whose every FP32 sum is exact (tests/nets.py, checked on the CPU), the kernel's
     logits equal the oracle's bit for bit, and its tuple is the first maximum; with a change of
     2^-8 planted in the oracle's last output bias, the comparison fails."""
@@ -138,7 +144,7 @@ def test_exact_networks_bit_for_bit(prec, case):
     ctx.load_model(rs, tg.pack_model(p, amax))
     h = wl.gen_trace(rules, [("inside", 2000), ("random", 309)], 41 + T)   # 18 tiles and a ragged one
     X = mlp.features(h)
-    z, tup = infer(ctx, rs, h, T, PREC[prec])
+    z, tup = infer(ctx, rs, h, T, PREC[prec], variant)
     z_or, _ = lowp(prec, p, X, amax)
     assert (z_or.astype(np.float32).astype(np.float64) == z_or).all()      # the oracle's values are FP32 values
     bad = np.argwhere(z.astype(np.float64) != z_or)
@@ -153,32 +159,34 @@ def test_exact_networks_bit_for_bit(prec, case):
     ctx.close()
 
 
+@pytest.mark.parametrize("variant", VARIANTS)
 @pytest.mark.parametrize("path", ["fused_bf16", "staged_bf16", "fused_fp8", "staged_fp8"])
-def test_ids_exact(setup, path):
+def test_ids_exact(setup, path, variant):
     ctx, rules, rs, T, p, amax, h = setup
     want = oc.classify(rules, h)
     d = to_dev(h)
     ids = ids_dev(len(h))
-    st = ctx.classify(rs, d, ids, path=path, stats=True)
+    st = ctx.classify(rs, d, ids, path=path, stats=True, variant=variant)
     assert (ids_host(ids) == want).all()
     assert st["packets"] == len(h)
     assert st["pred_hit"] + st["fallback"] == len(h)
 
 
-def test_ragged_sizes_and_graph(setup):
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_ragged_sizes_and_graph(setup, variant):
     ctx, rules, rs, T, p, amax, h = setup
     for n in (1, 5, 127, 128, 129, 255, 256, 257, 1000, 148 * 128 + 3, 74 * 256 + 129):
         hs = h[:n]
         d = to_dev(hs)
         ids = ids_dev(n)
-        ctx.classify(rs, d, ids, path="fused_bf16")
+        ctx.classify(rs, d, ids, path="fused_bf16", variant=variant)
         torch.cuda.synchronize()
         assert (ids_host(ids) == oc.classify(rules, hs)).all(), n
     d = to_dev(h)
     want = oc.classify(rules, h)
     for _ in range(3):
         ids = ids_dev(len(h))
-        ctx.classify(rs, d, ids, path="fused_bf16", graph=True)
+        ctx.classify(rs, d, ids, path="fused_bf16", graph=True, variant=variant)
         torch.cuda.synchronize()
         assert (ids_host(ids) == want).all()
 
@@ -209,19 +217,21 @@ def test_other_shapes(width, blocks):
     amax = calibrate(p, X)
     ctx.load_model(rs, tg.pack_model(p, amax))
     for prec in ("bf16", "fp8"):
-        z, tup = infer(ctx, rs, h[:4096], T, PREC[prec])
         z_or, mag = lowp(prec, p, X, amax)
-        stats, ok = compare_logits(z, z_or, mag, K=width, rho=RHO[prec])
-        print(width, blocks, prec, stats)
-        assert accepted(stats, ok, prec), (prec, stats)
-        assert (tup == np.argmax(z, axis=1)).all()
+        for variant in VARIANTS:
+            z, tup = infer(ctx, rs, h[:4096], T, PREC[prec], variant)
+            stats, ok = compare_logits(z, z_or, mag, K=width, rho=RHO[prec])
+            print(width, blocks, prec, variant, stats)
+            assert accepted(stats, ok, prec), (prec, variant, stats)
+            assert (tup == np.argmax(z, axis=1)).all()
     want = oc.classify(rules, h)
     d = to_dev(h)
-    for path in ("fused_bf16", "fused_fp8", "staged_bf16", "plain_fp32"):
+    for path, variant in (("fused_bf16", "n256"), ("fused_fp8", "n256"), ("fused_bf16", "pair"),
+                          ("fused_fp8", "pair"), ("staged_bf16", None), ("plain_fp32", None)):
         ids = ids_dev(len(h))
-        ctx.classify(rs, d, ids, path=path)
+        ctx.classify(rs, d, ids, path=path, variant=variant)
         torch.cuda.synchronize()
-        assert (ids_host(ids) == want).all(), path
+        assert (ids_host(ids) == want).all(), (path, variant)
     ctx.close()
 
 
@@ -242,12 +252,13 @@ def test_many_tuples(n_rules, width):
     amax = calibrate(p, X)
     ctx.load_model(rs, tg.pack_model(p, amax))
     for prec in ("bf16", "fp8"):
-        z, tup = infer(ctx, rs, h[:4096], T, PREC[prec])
         z_or, mag = lowp(prec, p, X, amax)
-        stats, ok = compare_logits(z, z_or, mag, K=width, rho=RHO[prec])
-        print(n_rules, width, prec, stats)
-        assert accepted(stats, ok, prec), (prec, stats)
-        assert (tup == np.argmax(z, axis=1)).all()
+        for variant in VARIANTS:
+            z, tup = infer(ctx, rs, h[:4096], T, PREC[prec], variant)
+            stats, ok = compare_logits(z, z_or, mag, K=width, rho=RHO[prec])
+            print(n_rules, width, prec, variant, stats)
+            assert accepted(stats, ok, prec), (prec, variant, stats)
+            assert (tup == np.argmax(z, axis=1)).all()
         if T > 256:
             # a 1 % shift of the second output chunk's biases in the oracle is caught
             q = dict(p)
@@ -257,9 +268,10 @@ def test_many_tuples(n_rules, width):
             assert not accepted(*compare_logits(z, zq, mq, K=width, rho=RHO[prec]), prec)
     want = oc.classify(rules, h)
     d = to_dev(h)
-    for path in ("fused_bf16", "fused_fp8", "staged_bf16", "plain_fp32"):
+    for path, variant in (("fused_bf16", "n256"), ("fused_fp8", "n256"), ("fused_bf16", "pair"),
+                          ("fused_fp8", "pair"), ("staged_bf16", None), ("plain_fp32", None)):
         ids = ids_dev(len(h))
-        ctx.classify(rs, d, ids, path=path)
+        ctx.classify(rs, d, ids, path=path, variant=variant)
         torch.cuda.synchronize()
-        assert (ids_host(ids) == want).all(), path
+        assert (ids_host(ids) == want).all(), (path, variant)
     ctx.close()
