@@ -71,7 +71,8 @@ constexpr int kArgG = 3;
 
 // Shared memory: for BF16 u (the FC1 output as swizzled K-blocks of 128 rows x 128 bytes; its
 // first 16 KB also hold the next tile's layer-0 operand between the last FC2 and the next FC1
-// epilogue), for FP8 (u in TMEM) the layer-0 operand alone; the weight stages, the predicted-tuple handoff to the search warps, the barriers, the partial argmax.
+// epilogue), for FP8 (u in TMEM) the layer-0 operand alone; the weight stages, the
+// predicted-tuple handoff to the search warps, the barriers, the partial argmax.
 // P: the CTA-pair kernel, whose CTAs each hold half of every 256-row weight tile (16 KB stages;
 // the freed shared memory buys deeper weight pipelines).
 template <bool F8, int HID, bool P = false>
@@ -137,7 +138,10 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
     constexpr int KBW = F8 ? 128 : 64;  // K per weight stage: 128 bytes of a row
     constexpr int KB = HID / KBW;       // K-blocks per layer
     constexpr int NCH = HID / 256;      // 256-column chunks per layer
-    constexpr uint32_t kActArrivals = F8 ? 8 : 4;  // 64-column units per K-block x 4 lane quadrants
+    // Arrivals per K-block of the next layer's input: one per 32-column piece x 4 lane quadrants
+    // (the hidden-layer epilogue publishes 32 columns at a time; layer 0 arrives twice per
+    // 64-column unit)
+    constexpr uint32_t kActArrivals = F8 ? 16 : 8;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
@@ -420,7 +424,7 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
         // ---------------- 16 epilogue warps ----------------
         const int ew = warp - kWarpEpi;
         const int q = warp & 3;   // TMEM lane quadrant
-        const int g = ew >> 2;    // 64-column unit of every 256-column chunk
+        const int g = ew >> 2;    // column group: layer 0 unit g of each chunk, hidden layers 32 g.. of each half
         const int r = q * 32 + lane;
         const uint32_t lane_base = uint32_t(q * 32) << 16;
         const float *sa = p.sa;
@@ -496,7 +500,7 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
         };
 
         // Per-column constants of the hidden layers, one per lane: the bias (FP8: b * s_out) of
-        // columns unit * 64 + lane and unit * 64 + 32 + lane; for FP8 also the layer's scale
+        // columns 256 c + 32 g + lane and 256 c + 128 + 32 g + lane; for FP8 also the layer's scale
         // dq * s_out, the same for every column (the hidden layers have one weight scale each).
         // Shuffles broadcast them across the warp's rows. They are loaded one chunk ahead: loads
         // issued at the chunk's start stalled the FP8 epilogue, which runs behind the MMAs and so
@@ -507,9 +511,9 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
             float b0, b1, d;
         };
         auto load_cc = [&](int L, int c) -> ColConst {
-            const int col = (4 * c + g) * 64 + lane;
+            const int col = 256 * c + 32 * g + lane;
             const float *bv = F8 ? p.fold8 + size_t(nl + L) * HID : p.bias + size_t(L) * HID;
-            return ColConst{__ldg(bv + col), __ldg(bv + col + 32), F8 ? __ldg(p.fold8 + size_t(L) * HID) : 0.f};
+            return ColConst{__ldg(bv + col), __ldg(bv + col + 128), F8 ? __ldg(p.fold8 + size_t(L) * HID) : 0.f};
         };
         ColConst next_cc = load_cc(0, 0);
         if (g == 0 && pt_first < n_pt) write_features(tile_of(pt_first));
@@ -535,6 +539,7 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
                 emit(reinterpret_cast<const float *>(a1), unit * 64 + 32, true);
                 ptx::tmem_wait_st();
                 act_arrive(unit * 64);
+                act_arrive(unit * 64 + 32);
             }
             if (!ok) break;
             // ---- hidden layers, NCH 256-column chunks each
@@ -543,11 +548,20 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
                 // BF16: v = acc + b. FP8: v = acc * (dq * s_out) + b * s_out, in the output's units.
                 // FP8 residual: x is stored in the units of its own layer input (scale s[L-1])
                 const float rr = F8 && fc2 ? sa[L + 1] / sa[L - 1] : 1.f;
+                // rr as FP16 bits when exact there (a power of two in [2^-24, 2^15]), else 0
+                uint32_t rr16 = 0;
+                if (F8 && fc2) {
+                    const __half h = __float2half_rn(rr);
+                    if (__half2float(h) == rr) rr16 = __half_as_ushort(h);
+                }
                 for (int c = 0; c < NCH; ++c, ++uses) {
                     [[maybe_unused]] const bool tr = lane == 0 && q == 2 && g < 2 && uses < uint32_t(trace::kChunks);
                     [[maybe_unused]] const int tslot = trace::kEpi + (g * trace::kChunks + int(uses)) * 4;
                     TC_TRACE(tslot + 0, tr);
-                    const int unit = 4 * c + g;
+                    // Warp g takes columns 32 g .. 32 g + 31 of each 128-column half of the chunk,
+                    // the first half before the second: the first half's K-blocks of the next
+                    // layer's input are published about halfway through the chunk's epilogue, so
+                    // that the next layer's first MMAs wait less at a layer boundary.
                     // this chunk's column constants, loaded one chunk ago; now the next chunk's
                     const ColConst cc = next_cc;
                     next_cc = c + 1 < NCH ? load_cc(L, c + 1) : load_cc(L + 1 < nl ? L + 1 : 0, 0);
@@ -559,8 +573,8 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
                     TC_TRACE(tslot + 1, tr);
                     ptx::tc_fence_after();
                     uint32_t a0[32], a1[32];
-                    ptx::tmem_ld32(tmem + lane_base + g * 64, a0);
-                    ptx::tmem_ld32(tmem + lane_base + g * 64 + 32, a1);
+                    ptx::tmem_ld32(tmem + lane_base + g * 32, a0);
+                    ptx::tmem_ld32(tmem + lane_base + 128 + g * 32, a1);
                     ptx::tmem_wait_ld();
                     // the accumulator may take the next chunk's MMAs now
                     ptx::tc_fence_before();
@@ -569,7 +583,7 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
                     TC_TRACE(tslot + 2, tr);
 #pragma unroll
                     for (int s = 0; s < 2; ++s) {
-                        const int col0 = unit * 64 + s * 32;
+                        const int col0 = 256 * c + 128 * s + 32 * g;
                         const uint32_t *a = s == 0 ? a0 : a1;
                         const float bl = s == 0 ? cc.b0 : cc.b1;
                         // two columns per packed f32x2 instruction: v = acc + b (BF16), acc * d + b (FP8)
@@ -585,19 +599,30 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
                         }
                         TC_TRACE(trace::kEpiX + (g * trace::kChunks + int(uses)) * 6 + 3 * s + 0, tr);
                         if (fc2) {
+                            // the residual x, one mixed-precision addition (BF16) or FMA (FP8, the
+                            // E4M3 codes widened to FP16 and rr given as FP16) per element
                             if (!F8) {
                                 uint32_t xr[16];
                                 ptx::tmem_ld16(x_col(col0), xr);
                                 ptx::tmem_wait_ld();
 #pragma unroll
                                 for (int j = 0; j < 16; ++j) {
-                                    const float2 r = add_f2(make_float2(v[2 * j], v[2 * j + 1]),
-                                                            make_float2(__uint_as_float(xr[j] << 16),
-                                                                        __uint_as_float(xr[j] & 0xFFFF0000u)));
-                                    v[2 * j] = r.x;
-                                    v[2 * j + 1] = r.y;
+                                    v[2 * j] = add_bf16lo(xr[j], v[2 * j]);
+                                    v[2 * j + 1] = add_bf16hi(xr[j], v[2 * j + 1]);
                                 }
-                            } else {
+                            } else if (rr16) {
+                                uint32_t xr[8];
+                                ptx::tmem_ld8(x_col(col0), xr);
+                                ptx::tmem_wait_ld();
+#pragma unroll
+                                for (int j = 0; j < 8; ++j) {
+                                    const uint32_t h01 = e4m3x2_to_h2(xr[j]), h23 = e4m3x2_to_h2(xr[j] >> 16);
+                                    v[4 * j + 0] = fma_f16lo(h01, rr16, v[4 * j + 0]);
+                                    v[4 * j + 1] = fma_f16hi(h01, rr16, v[4 * j + 1]);
+                                    v[4 * j + 2] = fma_f16lo(h23, rr16, v[4 * j + 2]);
+                                    v[4 * j + 3] = fma_f16hi(h23, rr16, v[4 * j + 3]);
+                                }
+                            } else {  // rr outside FP16's powers of two: widen to FP32
                                 uint32_t xr[8];
                                 ptx::tmem_ld8(x_col(col0), xr);
                                 ptx::tmem_wait_ld();
@@ -615,13 +640,13 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
                         }
                         TC_TRACE(trace::kEpiX + (g * trace::kChunks + int(uses)) * 6 + 3 * s + 1, tr);
                         emit(v, col0, fc2);
+                        if (fc2 || F8)
+                            ptx::tmem_wait_st();
+                        else
+                            ptx::fence_proxy_async_smem();
+                        act_arrive(col0);
                         TC_TRACE(trace::kEpiX + (g * trace::kChunks + int(uses)) * 6 + 3 * s + 2, tr);
                     }
-                    if (fc2 || F8)
-                        ptx::tmem_wait_st();
-                    else
-                        ptx::fence_proxy_async_smem();
-                    act_arrive(unit * 64);
                     TC_TRACE(tslot + 3, tr);
                     // after the last FC2 chunk (its MMAs, the last readers of u, have completed):
                     // the next tile's layer-0 operand
@@ -773,6 +798,7 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
         __syncthreads();
     ptx::tc_fence_after();
     if (warp == kWarpMma) {
+        __syncwarp();  // lane 0 issued the MMAs alone: converge before the warp-wide dealloc
         if (P)
             ptx::tmem_dealloc_cg2(tmem, 512);
         else

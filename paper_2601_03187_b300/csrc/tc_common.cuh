@@ -79,6 +79,39 @@ __device__ __forceinline__ float2 fma_f2(float2 a, float2 b, float2 c) {
     return f2_unpack(d);
 }
 
+// Residual additions in one mixed-precision instruction per element (the 16-bit operand widened
+// exactly, one rounding of the sum, as the unpack-then-add they replace): c + the BF16 in the low
+// or high half of `two`, and c + h * s for the FP16 in the low or high half of `two` and the FP16
+// in the low half of `s16`.
+__device__ __forceinline__ float add_bf16lo(uint32_t two, float c) {
+    float d;
+    asm("{\n\t.reg .b16 lo, hi;\n\tmov.b32 {lo, hi}, %1;\n\tadd.rn.f32.bf16 %0, lo, %2;\n\t}" : "=f"(d) : "r"(two), "f"(c));
+    return d;
+}
+__device__ __forceinline__ float add_bf16hi(uint32_t two, float c) {
+    float d;
+    asm("{\n\t.reg .b16 lo, hi;\n\tmov.b32 {lo, hi}, %1;\n\tadd.rn.f32.bf16 %0, hi, %2;\n\t}" : "=f"(d) : "r"(two), "f"(c));
+    return d;
+}
+__device__ __forceinline__ float fma_f16lo(uint32_t two, uint32_t s16, float c) {
+    float d;
+    asm("{\n\t.reg .b16 lo, hi, s, t;\n\tmov.b32 {lo, hi}, %1;\n\tmov.b32 {s, t}, %2;\n\tfma.rn.f32.f16 %0, lo, s, %3;\n\t}"
+        : "=f"(d) : "r"(two), "r"(s16), "f"(c));
+    return d;
+}
+__device__ __forceinline__ float fma_f16hi(uint32_t two, uint32_t s16, float c) {
+    float d;
+    asm("{\n\t.reg .b16 lo, hi, s, t;\n\tmov.b32 {lo, hi}, %1;\n\tmov.b32 {s, t}, %2;\n\tfma.rn.f32.f16 %0, hi, s, %3;\n\t}"
+        : "=f"(d) : "r"(two), "r"(s16), "f"(c));
+    return d;
+}
+// Four E4M3 codes (bits 0-7, 8-15 of `two`) as FP16x2, exactly.
+__device__ __forceinline__ uint32_t e4m3x2_to_h2(uint32_t two) {
+    uint32_t h2;
+    asm("cvt.rn.f16x2.e4m3x2 %0, %1;" : "=r"(h2) : "h"(uint16_t(two & 0xFFFFu)));
+    return h2;
+}
+
 // ReLU, round to nearest even and pack two BF16: lo in bits 0-15, hi in bits 16-31.
 __device__ __forceinline__ uint32_t relu_bf16x2(float lo, float hi) {
     uint32_t d;

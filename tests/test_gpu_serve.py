@@ -230,6 +230,6 @@ def test_tuned_shapes_restore_in_a_new_context():
             ctx.classify(rs, d, ids, path=path, graph=True)
             torch.cuda.synchronize()
             assert (ids_host(ids) == want).all(), path
-        for bad in ({"variant": 6}, {"grid": 100000}, {"search_threads": 96}, {"search_threads": 512, "search_bps": 8}):
+        for bad in ({"variant": 7}, {"variant": 1}, {"grid": 100000}, {"search_threads": 96}, {"search_threads": 512, "search_bps": 8}):
             with pytest.raises(tg.TangError):
                 ctx.autotune_set(rs, "no_nn", **bad)
