@@ -56,6 +56,9 @@ constexpr int kThreads = 32 * (kWarpSearch + kNumSearchWarps);  // 768
 // until decreases have freed enough), per sub-partition as well as per CTA.
 constexpr int kRegLaunch = 80, kRegCtl = 40, kRegEpi = 96, kRegSearch = 56;
 static_assert(kRegCtl + 4 * kRegEpi + kRegSearch == 6 * kRegLaunch, "register split must match the launch total");
+static_assert(kRegCtl <= kRegLaunch && kRegSearch <= kRegLaunch && kRegEpi >= kRegLaunch,
+              "setmaxnreg.dec may only lower and setmaxnreg.inc only raise a warp's registers");
+static_assert(kRegCtl % 8 == 0 && kRegEpi % 8 == 0 && kRegSearch % 8 == 0, "setmaxnreg takes multiples of 8");
 static_assert(kThreads * kRegLaunch <= 65536, "register file");
 constexpr uint64_t kTimeoutNs = 2000000000ull;
 constexpr uint32_t kXCol = 256;
@@ -277,10 +280,12 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
                 }
         }
     } else if (warp == kWarpMma) {
-        // One thread issues every MMA (in a pair, the first CTA's, for both). Plain loops over
-        // register state: this warp's issue rate bounds the tensor pipe's, so it keeps no state in
-        // captured lambdas or local memory.
-        if (lane == 0 && rank == 0) {
+        // The whole warp runs the issuing loop and lane 0 issues every MMA and commit (in a pair,
+        // the first CTA's warp, for both CTAs): run by all lanes, the loop's descriptors and TMEM
+        // addresses are warp-uniform. Plain loops over register state: this warp's issue rate
+        // bounds the tensor pipe's, so it keeps no state in captured lambdas or local memory.
+        if (rank == 0) {
+            const uint32_t lead = lane == 0;
             constexpr uint32_t kMmaM = P ? 256 : 128;
             const uint32_t idesc_h = ptx::idesc_make(kMmaM, 256, F8);
             const uint32_t idesc_0 = ptx::idesc_make(kMmaM, 256, false);  // layer 0: BF16 on both paths
@@ -313,25 +318,25 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
 #pragma unroll
                     for (int kk = 0; kk < kL0Kused / 16; ++kk) {
                         if (P)
-                            ptx::mma2_ss(tmem, a0_desc + 2 * kk, bd + 2 * kk, idesc_0, kk != 0, false);
+                            ptx::mma2_ss_l(lead, tmem, a0_desc + 2 * kk, bd + 2 * kk, idesc_0, kk != 0, false);
                         else
-                            ptx::mma_ss(tmem, a0_desc + 2 * kk, bd + 2 * kk, idesc_0, kk != 0, false);
+                            ptx::mma_ss_l(lead, tmem, a0_desc + 2 * kk, bd + 2 * kk, idesc_0, kk != 0, false);
                     }
                     if (P) {
-                        ptx::mma2_commit(ptx::smem_u32(&empty[stage]));
-                        ptx::mma2_commit(ptx::smem_u32(&empty[stage]) + peer_off);
+                        ptx::mma2_commit_l(lead, ptx::smem_u32(&empty[stage]));
+                        ptx::mma2_commit_l(lead, ptx::smem_u32(&empty[stage]) + peer_off);
                     } else {
-                        ptx::mma_commit(&empty[stage]);
+                        ptx::mma_commit_l(lead, &empty[stage]);
                     }
                     if (++stage == kStages) {
                         stage = 0;
                         phase ^= 1;
                     }
                     if (P) {
-                        ptx::mma2_commit(ptx::smem_u32(acc_full));
-                        ptx::mma2_commit(ptx::smem_u32(acc_full) + peer_off);
+                        ptx::mma2_commit_l(lead, ptx::smem_u32(acc_full));
+                        ptx::mma2_commit_l(lead, ptx::smem_u32(acc_full) + peer_off);
                     } else {
-                        ptx::mma_commit(acc_full);
+                        ptx::mma_commit_l(lead, acc_full);
                     }
                     TC_TRACE(trace::kMma + uses * 12 + 10, uses < uint32_t(trace::kChunks));
                 }
@@ -365,34 +370,34 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
 #pragma unroll
                                 for (int kk = 0; kk < 4; ++kk) {
                                     if (P)
-                                        ptx::mma2_ts(tmem, ta + kk * 8, bd + 2 * kk, idesc, (kb | kk) != 0, F8);
+                                        ptx::mma2_ts_l(lead, tmem, ta + kk * 8, bd + 2 * kk, idesc, (kb | kk) != 0, F8);
                                     else
-                                        ptx::mma_ts(tmem, ta + kk * 8, bd + 2 * kk, idesc, (kb | kk) != 0, F8);
+                                        ptx::mma_ts_l(lead, tmem, ta + kk * 8, bd + 2 * kk, idesc, (kb | kk) != 0, F8);
                                 }
                             } else if (F8) {  // FC2, FP8: A = u from TMEM
                                 const uint32_t ta = tmem + kUCol + kb * 32;
 #pragma unroll
                                 for (int kk = 0; kk < 4; ++kk) {
                                     if (P)
-                                        ptx::mma2_ts(tmem, ta + kk * 8, bd + 2 * kk, idesc, (kb | kk) != 0, F8);
+                                        ptx::mma2_ts_l(lead, tmem, ta + kk * 8, bd + 2 * kk, idesc, (kb | kk) != 0, F8);
                                     else
-                                        ptx::mma_ts(tmem, ta + kk * 8, bd + 2 * kk, idesc, (kb | kk) != 0, F8);
+                                        ptx::mma_ts_l(lead, tmem, ta + kk * 8, bd + 2 * kk, idesc, (kb | kk) != 0, F8);
                                 }
                             } else {  // FC2, BF16: A = u from shared memory
                                 const uint64_t ad = a0_desc + uint64_t(kb) * (16384 >> 4);
 #pragma unroll
                                 for (int kk = 0; kk < 4; ++kk) {
                                     if (P)
-                                        ptx::mma2_ss(tmem, ad + 2 * kk, bd + 2 * kk, idesc, (kb | kk) != 0, F8);
+                                        ptx::mma2_ss_l(lead, tmem, ad + 2 * kk, bd + 2 * kk, idesc, (kb | kk) != 0, F8);
                                     else
-                                        ptx::mma_ss(tmem, ad + 2 * kk, bd + 2 * kk, idesc, (kb | kk) != 0, F8);
+                                        ptx::mma_ss_l(lead, tmem, ad + 2 * kk, bd + 2 * kk, idesc, (kb | kk) != 0, F8);
                                 }
                             }
                             if (P) {
-                                ptx::mma2_commit(ptx::smem_u32(&empty[stage]));
-                                ptx::mma2_commit(ptx::smem_u32(&empty[stage]) + peer_off);
+                                ptx::mma2_commit_l(lead, ptx::smem_u32(&empty[stage]));
+                                ptx::mma2_commit_l(lead, ptx::smem_u32(&empty[stage]) + peer_off);
                             } else {
-                                ptx::mma_commit(&empty[stage]);
+                                ptx::mma_commit_l(lead, &empty[stage]);
                             }
                             if (++stage == kStages) {
                                 stage = 0;
@@ -401,10 +406,10 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
                         }
                         if (err) break;
                         if (P) {
-                            ptx::mma2_commit(ptx::smem_u32(acc_full));
-                            ptx::mma2_commit(ptx::smem_u32(acc_full) + peer_off);
+                            ptx::mma2_commit_l(lead, ptx::smem_u32(acc_full));
+                            ptx::mma2_commit_l(lead, ptx::smem_u32(acc_full) + peer_off);
                         } else {
-                            ptx::mma_commit(acc_full);
+                            ptx::mma_commit_l(lead, acc_full);
                         }
                         TC_TRACE(trace::kMma + uses * 12 + 10, uses < uint32_t(trace::kChunks));
                     }
@@ -413,9 +418,9 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
             if (err) fail(err);
             volatile int never = 0;
             if (P)
-                ptx::mma2_commit(ptx::smem_u32(drain));
+                ptx::mma2_commit_l(lead, ptx::smem_u32(drain));
             else
-                ptx::mma_commit(drain);
+                ptx::mma_commit_l(lead, drain);
             ptx::mbar_wait(drain, 0, &never, kTimeoutNs);
         }
     }  // warps 2 and 3 of the control group have no role
