@@ -200,6 +200,13 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
         else
             ptx::mbar_arrive(b);
     };
+    // the accumulator release: in a pair a relaxed arrive (see mbar_arrive_cluster_relaxed)
+    auto release_acc = [&]() {
+        if (P)
+            ptx::mbar_arrive_cluster_relaxed(lead(acc_empty));
+        else
+            ptx::mbar_arrive(acc_empty);
+    };
     // waits on barriers that receive arrivals or MMA commits from the other CTA of a pair
     auto wait_x = [&](uint64_t *b, uint32_t parity) {
         return P ? ptx::mbar_wait_cl(b, parity, sAbort, kTimeoutNs) : ptx::mbar_wait(b, parity, sAbort, kTimeoutNs);
@@ -539,7 +546,7 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
                 ptx::tmem_wait_ld();
                 ptx::tc_fence_before();
                 __syncwarp();
-                if (lane == 0) arrive_mma_side(acc_empty);
+                if (lane == 0) release_acc();
                 emit(reinterpret_cast<const float *>(a0), unit * 64, true);
                 emit(reinterpret_cast<const float *>(a1), unit * 64 + 32, true);
                 ptx::tmem_wait_st();
@@ -584,7 +591,7 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
                     // the accumulator may take the next chunk's MMAs now
                     ptx::tc_fence_before();
                     __syncwarp();
-                    if (lane == 0) arrive_mma_side(acc_empty);
+                    if (lane == 0) release_acc();
                     TC_TRACE(tslot + 2, tr);
 #pragma unroll
                     for (int s = 0; s < 2; ++s) {
@@ -696,7 +703,7 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
                     }
                     ptx::tc_fence_before();
                     __syncwarp();
-                    if (lane == 0) arrive_mma_side(acc_empty);
+                    if (lane == 0) release_acc();
                 }
                 if (!ok) break;
                 const uint32_t t = tcnt & 1, tu = tcnt >> 1;  // this CTA's tile count: barrier parities
