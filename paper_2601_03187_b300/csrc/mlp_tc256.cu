@@ -102,7 +102,7 @@ struct Layout {
 //
 // P (CTA pairs): the kernel runs in clusters of two CTAs on two SMs. Each CTA keeps its own
 // 128-packet tile, its own accumulator and x in its TMEM and its own u (BF16: shared memory, FP8: TMEM), but the
-// first CTA's MMA thread issues every MMA for both as one cta_group::2 MMA with M = 256: each CTA
+// first CTA's MMA warp issues every MMA for both as one cta_group::2 MMA with M = 256: each CTA
 // loads only its 128 rows (output columns) of each weight tile, so an SM streams and reads half
 // the weight bytes per MMA and issues no MMAs of its own half the time. The barriers the MMAs wait
 // on (stages full, accumulator drained, activations published) live in the first CTA and count
@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
     auto tile_of = [&](uint32_t pt) { return P ? 2 * pt + rank : pt; };
     // shared::cluster address of a barrier in the first CTA of the pair (this CTA's own otherwise)
     auto lead = [&](uint64_t *b) { return P ? ptx::mapa(ptx::smem_u32(b), 0) : ptx::smem_u32(b); };
-    // arrival on a barrier the MMA thread waits for
+    // arrival on a barrier the MMA warp waits for
     auto arrive_mma_side = [&](uint64_t *b) {
         if (P)
             ptx::mbar_arrive_cluster(lead(b));
@@ -810,7 +810,7 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
         __syncthreads();
     ptx::tc_fence_after();
     if (warp == kWarpMma) {
-        __syncwarp();  // lane 0 issued the MMAs alone: converge before the warp-wide dealloc
+        __syncwarp();  // the issue loop's bounded waits may have left the lanes apart: converge before the warp-wide dealloc
         if (P)
             ptx::tmem_dealloc_cg2(tmem, 512);
         else
