@@ -300,6 +300,7 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
             const uint32_t peer_off = P ? ptx::mapa(ptx::smem_u32(bars), 1) - ptx::smem_u32(bars) : 0u;
             const uint32_t y_addr = ptx::smem_u32(sY), st_addr = ptx::smem_u32(sStage);
             const uint64_t a0_desc = ptx::sdesc_sw128(y_addr);
+            const uint64_t bd0 = ptx::sdesc_sw128(st_addr);  // stage s: bd0 + s * kStageBytes / 16
             uint32_t stage = 0, phase = 0, uses = 0, lay = 0, ntile = 0;
             int err = 0;
             for (uint32_t pt = pt_first; pt < n_pt && !err; pt += pt_step, ++ntile) {
@@ -360,6 +361,9 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
                         }
                         TC_TRACE(trace::kMma + uses * 12 + 1, uses < uint32_t(trace::kChunks));
                         ptx::tc_fence_after();
+                        // unrolled by four: measured +3.5 % (BF16) and +1 % (FP8) over the rolled loop;
+                        // unrolling all eight BF16 K-blocks lost 8 %
+#pragma unroll 4
                         for (int kb = 0; kb < KB; ++kb) {
                             if (c == 0 && !wait_x(&act[kb], lay & 1)) {
                                 err = 4;
@@ -371,7 +375,7 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
                             }
                             TC_TRACE(trace::kMma + uses * 12 + 2 + kb, uses < uint32_t(trace::kChunks));
                             ptx::tc_fence_after();
-                            const uint64_t bd = ptx::sdesc_sw128(st_addr + stage * kStageBytes);
+                            const uint64_t bd = bd0 + uint64_t(stage * (kStageBytes >> 4));
                             if (a_tmem) {
                                 const uint32_t ta = tmem + kXCol + kb * 32;
 #pragma unroll
