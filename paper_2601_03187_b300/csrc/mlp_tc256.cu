@@ -292,7 +292,7 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
         // addresses are warp-uniform. Plain loops over register state: this warp's issue rate
         // bounds the tensor pipe's, so it keeps no state in captured lambdas or local memory.
         if (rank == 0) {
-            const uint32_t lead = lane == 0;
+            const uint32_t issuer = lane == 0;  // the lane that issues MMAs and commits
             constexpr uint32_t kMmaM = P ? 256 : 128;
             const uint32_t idesc_h = ptx::idesc_make(kMmaM, 256, F8);
             const uint32_t idesc_0 = ptx::idesc_make(kMmaM, 256, false);  // layer 0: BF16 on both paths
@@ -326,25 +326,25 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
 #pragma unroll
                     for (int kk = 0; kk < kL0Kused / 16; ++kk) {
                         if (P)
-                            ptx::mma2_ss_l(lead, tmem, a0_desc + 2 * kk, bd + 2 * kk, idesc_0, kk != 0, false);
+                            ptx::mma2_ss_l(issuer, tmem, a0_desc + 2 * kk, bd + 2 * kk, idesc_0, kk != 0, false);
                         else
-                            ptx::mma_ss_l(lead, tmem, a0_desc + 2 * kk, bd + 2 * kk, idesc_0, kk != 0, false);
+                            ptx::mma_ss_l(issuer, tmem, a0_desc + 2 * kk, bd + 2 * kk, idesc_0, kk != 0, false);
                     }
                     if (P) {
-                        ptx::mma2_commit_l(lead, ptx::smem_u32(&empty[stage]));
-                        ptx::mma2_commit_l(lead, ptx::smem_u32(&empty[stage]) + peer_off);
+                        ptx::mma2_commit_l(issuer, ptx::smem_u32(&empty[stage]));
+                        ptx::mma2_commit_l(issuer, ptx::smem_u32(&empty[stage]) + peer_off);
                     } else {
-                        ptx::mma_commit_l(lead, &empty[stage]);
+                        ptx::mma_commit_l(issuer, &empty[stage]);
                     }
                     if (++stage == kStages) {
                         stage = 0;
                         phase ^= 1;
                     }
                     if (P) {
-                        ptx::mma2_commit_l(lead, ptx::smem_u32(acc_full));
-                        ptx::mma2_commit_l(lead, ptx::smem_u32(acc_full) + peer_off);
+                        ptx::mma2_commit_l(issuer, ptx::smem_u32(acc_full));
+                        ptx::mma2_commit_l(issuer, ptx::smem_u32(acc_full) + peer_off);
                     } else {
-                        ptx::mma_commit_l(lead, acc_full);
+                        ptx::mma_commit_l(issuer, acc_full);
                     }
                     TC_TRACE(trace::kMma + uses * 12 + 10, uses < uint32_t(trace::kChunks));
                 }
@@ -381,34 +381,34 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
 #pragma unroll
                                 for (int kk = 0; kk < 4; ++kk) {
                                     if (P)
-                                        ptx::mma2_ts_l(lead, tmem, ta + kk * 8, bd + 2 * kk, idesc, (kb | kk) != 0, F8);
+                                        ptx::mma2_ts_l(issuer, tmem, ta + kk * 8, bd + 2 * kk, idesc, (kb | kk) != 0, F8);
                                     else
-                                        ptx::mma_ts_l(lead, tmem, ta + kk * 8, bd + 2 * kk, idesc, (kb | kk) != 0, F8);
+                                        ptx::mma_ts_l(issuer, tmem, ta + kk * 8, bd + 2 * kk, idesc, (kb | kk) != 0, F8);
                                 }
                             } else if (F8) {  // FC2, FP8: A = u from TMEM
                                 const uint32_t ta = tmem + kUCol + kb * 32;
 #pragma unroll
                                 for (int kk = 0; kk < 4; ++kk) {
                                     if (P)
-                                        ptx::mma2_ts_l(lead, tmem, ta + kk * 8, bd + 2 * kk, idesc, (kb | kk) != 0, F8);
+                                        ptx::mma2_ts_l(issuer, tmem, ta + kk * 8, bd + 2 * kk, idesc, (kb | kk) != 0, F8);
                                     else
-                                        ptx::mma_ts_l(lead, tmem, ta + kk * 8, bd + 2 * kk, idesc, (kb | kk) != 0, F8);
+                                        ptx::mma_ts_l(issuer, tmem, ta + kk * 8, bd + 2 * kk, idesc, (kb | kk) != 0, F8);
                                 }
                             } else {  // FC2, BF16: A = u from shared memory
                                 const uint64_t ad = a0_desc + uint64_t(kb) * (16384 >> 4);
 #pragma unroll
                                 for (int kk = 0; kk < 4; ++kk) {
                                     if (P)
-                                        ptx::mma2_ss_l(lead, tmem, ad + 2 * kk, bd + 2 * kk, idesc, (kb | kk) != 0, F8);
+                                        ptx::mma2_ss_l(issuer, tmem, ad + 2 * kk, bd + 2 * kk, idesc, (kb | kk) != 0, F8);
                                     else
-                                        ptx::mma_ss_l(lead, tmem, ad + 2 * kk, bd + 2 * kk, idesc, (kb | kk) != 0, F8);
+                                        ptx::mma_ss_l(issuer, tmem, ad + 2 * kk, bd + 2 * kk, idesc, (kb | kk) != 0, F8);
                                 }
                             }
                             if (P) {
-                                ptx::mma2_commit_l(lead, ptx::smem_u32(&empty[stage]));
-                                ptx::mma2_commit_l(lead, ptx::smem_u32(&empty[stage]) + peer_off);
+                                ptx::mma2_commit_l(issuer, ptx::smem_u32(&empty[stage]));
+                                ptx::mma2_commit_l(issuer, ptx::smem_u32(&empty[stage]) + peer_off);
                             } else {
-                                ptx::mma_commit_l(lead, &empty[stage]);
+                                ptx::mma_commit_l(issuer, &empty[stage]);
                             }
                             if (++stage == kStages) {
                                 stage = 0;
@@ -417,10 +417,10 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
                         }
                         if (err) break;
                         if (P) {
-                            ptx::mma2_commit_l(lead, ptx::smem_u32(acc_full));
-                            ptx::mma2_commit_l(lead, ptx::smem_u32(acc_full) + peer_off);
+                            ptx::mma2_commit_l(issuer, ptx::smem_u32(acc_full));
+                            ptx::mma2_commit_l(issuer, ptx::smem_u32(acc_full) + peer_off);
                         } else {
-                            ptx::mma_commit_l(lead, acc_full);
+                            ptx::mma_commit_l(issuer, acc_full);
                         }
                         TC_TRACE(trace::kMma + uses * 12 + 10, uses < uint32_t(trace::kChunks));
                     }
@@ -429,9 +429,9 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
             if (err) fail(err);
             volatile int never = 0;
             if (P)
-                ptx::mma2_commit_l(lead, ptx::smem_u32(drain));
+                ptx::mma2_commit_l(issuer, ptx::smem_u32(drain));
             else
-                ptx::mma_commit_l(lead, drain);
+                ptx::mma_commit_l(issuer, drain);
             ptx::mbar_wait(drain, 0, &never, kTimeoutNs);
         }
     }  // warps 2 and 3 of the control group have no role
