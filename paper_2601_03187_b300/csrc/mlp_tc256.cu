@@ -361,58 +361,122 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
                         }
                         TC_TRACE(trace::kMma + uses * 12 + 1, uses < uint32_t(trace::kChunks));
                         ptx::tc_fence_after();
-                        // unrolled by four: measured +3.5 % (BF16) and +1 % (FP8) over the rolled loop;
-                        // unrolling all eight BF16 K-blocks lost 8 %
-#pragma unroll 4
-                        for (int kb = 0; kb < KB; ++kb) {
-                            if (c == 0 && !wait_x(&act[kb], lay & 1)) {
-                                err = 4;
-                                break;
-                            }
-                            if (!wait_x(&full[stage], phase)) {
-                                err = 8;
-                                break;
-                            }
-                            TC_TRACE(trace::kMma + uses * 12 + 2 + kb, uses < uint32_t(trace::kChunks));
-                            ptx::tc_fence_after();
-                            const uint64_t bd = bd0 + uint64_t(stage * (kStageBytes >> 4));
+                        // The K-block loops, unrolled by four. BF16 has one loop per A source (x in
+                        // TMEM, u in shared memory), so each loop body holds one MMA form; FP8 keeps
+                        // one loop that chooses per K-block. Measured against one rolled loop: +3.5 %
+                        // (unrolled) then +7 % (split) for BF16, +1 % for FP8, whose split loops lost
+                        // 2.5 %; unrolling all eight BF16 K-blocks of the single loop lost 8 %.
+                        if constexpr (!F8) {
                             if (a_tmem) {
-                                const uint32_t ta = tmem + kXCol + kb * 32;
+#pragma unroll 4
+                                for (int kb = 0; kb < KB; ++kb) {
+                                    if (c == 0 && !wait_x(&act[kb], lay & 1)) {
+                                        err = 4;
+                                        break;
+                                    }
+                                    if (!wait_x(&full[stage], phase)) {
+                                        err = 8;
+                                        break;
+                                    }
+                                    TC_TRACE(trace::kMma + uses * 12 + 2 + kb, uses < uint32_t(trace::kChunks));
+                                    ptx::tc_fence_after();
+                                    const uint64_t bd = bd0 + uint64_t(stage * (kStageBytes >> 4));
+                                    const uint32_t ta = tmem + kXCol + kb * 32;
 #pragma unroll
-                                for (int kk = 0; kk < 4; ++kk) {
-                                    if (P)
-                                        ptx::mma2_ts_l(issuer, tmem, ta + kk * 8, bd + 2 * kk, idesc, (kb | kk) != 0, F8);
-                                    else
-                                        ptx::mma_ts_l(issuer, tmem, ta + kk * 8, bd + 2 * kk, idesc, (kb | kk) != 0, F8);
+                                    for (int kk = 0; kk < 4; ++kk) {
+                                        if (P)
+                                            ptx::mma2_ts_l(issuer, tmem, ta + kk * 8, bd + 2 * kk, idesc, (kb | kk) != 0, F8);
+                                        else
+                                            ptx::mma_ts_l(issuer, tmem, ta + kk * 8, bd + 2 * kk, idesc, (kb | kk) != 0, F8);
+                                    }
+                                    if (P) {
+                                        ptx::mma2_commit_l(issuer, ptx::smem_u32(&empty[stage]));
+                                        ptx::mma2_commit_l(issuer, ptx::smem_u32(&empty[stage]) + peer_off);
+                                    } else {
+                                        ptx::mma_commit_l(issuer, &empty[stage]);
+                                    }
+                                    if (++stage == kStages) {
+                                        stage = 0;
+                                        phase ^= 1;
+                                    }
                                 }
-                            } else if (F8) {  // FC2, FP8: A = u from TMEM
-                                const uint32_t ta = tmem + kUCol + kb * 32;
-#pragma unroll
-                                for (int kk = 0; kk < 4; ++kk) {
-                                    if (P)
-                                        ptx::mma2_ts_l(issuer, tmem, ta + kk * 8, bd + 2 * kk, idesc, (kb | kk) != 0, F8);
-                                    else
-                                        ptx::mma_ts_l(issuer, tmem, ta + kk * 8, bd + 2 * kk, idesc, (kb | kk) != 0, F8);
-                                }
-                            } else {  // FC2, BF16: A = u from shared memory
-                                const uint64_t ad = a0_desc + uint64_t(kb) * (16384 >> 4);
-#pragma unroll
-                                for (int kk = 0; kk < 4; ++kk) {
-                                    if (P)
-                                        ptx::mma2_ss_l(issuer, tmem, ad + 2 * kk, bd + 2 * kk, idesc, (kb | kk) != 0, F8);
-                                    else
-                                        ptx::mma_ss_l(issuer, tmem, ad + 2 * kk, bd + 2 * kk, idesc, (kb | kk) != 0, F8);
-                                }
-                            }
-                            if (P) {
-                                ptx::mma2_commit_l(issuer, ptx::smem_u32(&empty[stage]));
-                                ptx::mma2_commit_l(issuer, ptx::smem_u32(&empty[stage]) + peer_off);
                             } else {
-                                ptx::mma_commit_l(issuer, &empty[stage]);
+#pragma unroll 4
+                                for (int kb = 0; kb < KB; ++kb) {
+                                    if (c == 0 && !wait_x(&act[kb], lay & 1)) {
+                                        err = 4;
+                                        break;
+                                    }
+                                    if (!wait_x(&full[stage], phase)) {
+                                        err = 8;
+                                        break;
+                                    }
+                                    TC_TRACE(trace::kMma + uses * 12 + 2 + kb, uses < uint32_t(trace::kChunks));
+                                    ptx::tc_fence_after();
+                                    const uint64_t bd = bd0 + uint64_t(stage * (kStageBytes >> 4));
+                                    const uint64_t ad = a0_desc + uint64_t(kb) * (16384 >> 4);
+#pragma unroll
+                                    for (int kk = 0; kk < 4; ++kk) {
+                                        if (P)
+                                            ptx::mma2_ss_l(issuer, tmem, ad + 2 * kk, bd + 2 * kk, idesc, (kb | kk) != 0, F8);
+                                        else
+                                            ptx::mma_ss_l(issuer, tmem, ad + 2 * kk, bd + 2 * kk, idesc, (kb | kk) != 0, F8);
+                                    }
+                                    if (P) {
+                                        ptx::mma2_commit_l(issuer, ptx::smem_u32(&empty[stage]));
+                                        ptx::mma2_commit_l(issuer, ptx::smem_u32(&empty[stage]) + peer_off);
+                                    } else {
+                                        ptx::mma_commit_l(issuer, &empty[stage]);
+                                    }
+                                    if (++stage == kStages) {
+                                        stage = 0;
+                                        phase ^= 1;
+                                    }
+                                }
                             }
-                            if (++stage == kStages) {
-                                stage = 0;
-                                phase ^= 1;
+                        } else {
+#pragma unroll 4
+                            for (int kb = 0; kb < KB; ++kb) {
+                                if (c == 0 && !wait_x(&act[kb], lay & 1)) {
+                                    err = 4;
+                                    break;
+                                }
+                                if (!wait_x(&full[stage], phase)) {
+                                    err = 8;
+                                    break;
+                                }
+                                TC_TRACE(trace::kMma + uses * 12 + 2 + kb, uses < uint32_t(trace::kChunks));
+                                ptx::tc_fence_after();
+                                const uint64_t bd = bd0 + uint64_t(stage * (kStageBytes >> 4));
+                                if (a_tmem) {
+                                    const uint32_t ta = tmem + kXCol + kb * 32;
+#pragma unroll
+                                    for (int kk = 0; kk < 4; ++kk) {
+                                        if (P)
+                                            ptx::mma2_ts_l(issuer, tmem, ta + kk * 8, bd + 2 * kk, idesc, (kb | kk) != 0, F8);
+                                        else
+                                            ptx::mma_ts_l(issuer, tmem, ta + kk * 8, bd + 2 * kk, idesc, (kb | kk) != 0, F8);
+                                    }
+                                } else {  // FC2: A = u from TMEM
+                                    const uint32_t ta = tmem + kUCol + kb * 32;
+#pragma unroll
+                                    for (int kk = 0; kk < 4; ++kk) {
+                                        if (P)
+                                            ptx::mma2_ts_l(issuer, tmem, ta + kk * 8, bd + 2 * kk, idesc, (kb | kk) != 0, F8);
+                                        else
+                                            ptx::mma_ts_l(issuer, tmem, ta + kk * 8, bd + 2 * kk, idesc, (kb | kk) != 0, F8);
+                                    }
+                                }
+                                if (P) {
+                                    ptx::mma2_commit_l(issuer, ptx::smem_u32(&empty[stage]));
+                                    ptx::mma2_commit_l(issuer, ptx::smem_u32(&empty[stage]) + peer_off);
+                                } else {
+                                    ptx::mma_commit_l(issuer, &empty[stage]);
+                                }
+                                if (++stage == kStages) {
+                                    stage = 0;
+                                    phase ^= 1;
+                                }
                             }
                         }
                         if (err) break;
