@@ -361,11 +361,12 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
                         }
                         TC_TRACE(trace::kMma + uses * 12 + 1, uses < uint32_t(trace::kChunks));
                         ptx::tc_fence_after();
-                        // The K-block loops, unrolled by four. BF16 has one loop per A source (x in
-                        // TMEM, u in shared memory), so each loop body holds one MMA form; FP8 keeps
-                        // one loop that chooses per K-block. Measured against one rolled loop: +3.5 %
-                        // (unrolled) then +7 % (split) for BF16, +1 % for FP8, whose split loops lost
-                        // 2.5 %; unrolling all eight BF16 K-blocks of the single loop lost 8 %.
+                        // The K-block loops, unrolled by four, each body one MMA form. BF16 has one
+                        // loop per A source (x in TMEM, u in shared memory); FP8 reads both from TMEM,
+                        // so one loop takes the source's base column. Measured against one rolled loop
+                        // that chose the form per K-block: +3.5 % (unrolled) then +4-7 % (split) for
+                        // BF16, +1 % for FP8 (+4 % more without the choice, network alone); two split
+                        // FP8 loops lost 2.5 %, and unrolling all eight BF16 K-blocks lost 8 %.
                         if constexpr (!F8) {
                             if (a_tmem) {
 #pragma unroll 4
@@ -435,6 +436,7 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
                                 }
                             }
                         } else {
+                            const uint32_t a_base = tmem + (a_tmem ? kXCol : kUCol);  // x (FC1, output) or u (FC2)
 #pragma unroll 4
                             for (int kb = 0; kb < KB; ++kb) {
                                 if (c == 0 && !wait_x(&act[kb], lay & 1)) {
@@ -448,24 +450,13 @@ __global__ void __launch_bounds__(tc256::kThreads, 1)
                                 TC_TRACE(trace::kMma + uses * 12 + 2 + kb, uses < uint32_t(trace::kChunks));
                                 ptx::tc_fence_after();
                                 const uint64_t bd = bd0 + uint64_t(stage * (kStageBytes >> 4));
-                                if (a_tmem) {
-                                    const uint32_t ta = tmem + kXCol + kb * 32;
+                                const uint32_t ta = a_base + kb * 32;
 #pragma unroll
-                                    for (int kk = 0; kk < 4; ++kk) {
-                                        if (P)
-                                            ptx::mma2_ts_l(issuer, tmem, ta + kk * 8, bd + 2 * kk, idesc, (kb | kk) != 0, F8);
-                                        else
-                                            ptx::mma_ts_l(issuer, tmem, ta + kk * 8, bd + 2 * kk, idesc, (kb | kk) != 0, F8);
-                                    }
-                                } else {  // FC2: A = u from TMEM
-                                    const uint32_t ta = tmem + kUCol + kb * 32;
-#pragma unroll
-                                    for (int kk = 0; kk < 4; ++kk) {
-                                        if (P)
-                                            ptx::mma2_ts_l(issuer, tmem, ta + kk * 8, bd + 2 * kk, idesc, (kb | kk) != 0, F8);
-                                        else
-                                            ptx::mma_ts_l(issuer, tmem, ta + kk * 8, bd + 2 * kk, idesc, (kb | kk) != 0, F8);
-                                    }
+                                for (int kk = 0; kk < 4; ++kk) {
+                                    if (P)
+                                        ptx::mma2_ts_l(issuer, tmem, ta + kk * 8, bd + 2 * kk, idesc, (kb | kk) != 0, F8);
+                                    else
+                                        ptx::mma_ts_l(issuer, tmem, ta + kk * 8, bd + 2 * kk, idesc, (kb | kk) != 0, F8);
                                 }
                                 if (P) {
                                     ptx::mma2_commit_l(issuer, ptx::smem_u32(&empty[stage]));
