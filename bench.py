@@ -609,8 +609,9 @@ def long_run_rules(n_plain, n_wild, seed):
 
 def measure_long_runs(tg, ctx, n_packets=1 << 20):
     """512k rules plus 8,192 rules under tuple (0,0) (one run of more than 8k rules under one key),
-    1M packets: the search alone and the fused BF16 path, each with the warp-cooperative scan of
-    long runs and with one thread per run (TANG_SEARCH_SERIAL); ids against the oracle."""
+    1M packets: the search alone and the fused BF16 kernel, each with the warp-cooperative scan of
+    long runs and with one thread per run (TANG_SEARCH_SERIAL); the fused path as two kernels
+    (TANG_FUSED_SPLIT) and in the form the autotuner picks; ids against the oracle."""
     import torch
     from oracle import classify as oc
     rules = long_run_rules(N_RULES, 8192, 17)
@@ -622,20 +623,28 @@ def measure_long_runs(tg, ctx, n_packets=1 << 20):
     want = oc.classify(rules, h)
     out = {"rules": len(rules), "run_00": int(((rules["sip_len"] == 0) & (rules["dip_len"] == 0)).sum()),
            "packets": len(h)}
+    def timed(key, path, serial=False, variant=None):
+        for _ in range(3):
+            ctx.classify(rs, d, ids, path=path, graph=True, serial=serial, variant=variant)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(5):
+            ctx.classify(rs, d, ids, path=path, graph=True, serial=serial, variant=variant)
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / 5
+        st = ctx.classify(rs, d, ids, path=path, stats=True, serial=serial, variant=variant)
+        out[key] = {"mpkts": round(len(h) / dt / 1e6, 3), "rule_reads_per_pkt": round(st["rule_reads"] / len(h), 3),
+                    "ids_equal_oracle": bool((ids.cpu().numpy().view(np.uint32) == want).all())}
+
     for path in ("no_nn", "fused_bf16"):
         for serial in (False, True):
-            for _ in range(3):
-                ctx.classify(rs, d, ids, path=path, graph=True, serial=serial)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            for _ in range(5):
-                ctx.classify(rs, d, ids, path=path, graph=True, serial=serial)
-            torch.cuda.synchronize()
-            dt = (time.perf_counter() - t0) / 5
-            st = ctx.classify(rs, d, ids, path=path, stats=True, serial=serial)
-            out["%s_%s" % (path, "serial" if serial else "warp")] = {
-                "mpkts": round(len(h) / dt / 1e6, 3), "rule_reads_per_pkt": round(st["rule_reads"] / len(h), 3),
-                "ids_equal_oracle": bool((ids.cpu().numpy().view(np.uint32) == want).all())}
+            timed("%s_%s" % (path, "serial" if serial else "warp"), path, serial, "n256" if path != "no_nn" else None)
+    # the fused path as two kernels (network, then the search with the whole GPU), and the form
+    # the autotuner picks on this batch
+    timed("fused_bf16_split", "fused_bf16", variant="split")
+    ctx.autotune(rs, d, path="fused_bf16")
+    timed("fused_bf16_autotuned", "fused_bf16")
+    out["fused_bf16_autotuned"]["variant"] = ctx.autotune_get(rs, "fused_bf16")["variant"]
     ctx.unload_ruleset(rs)
     return out
 

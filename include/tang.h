@@ -191,6 +191,12 @@ int tang_load_model(tang_ctx *ctx, uint32_t rs, const void *blob, size_t bytes);
 #define TANG_FUSED_N256 0x2000    /* one CTA per SM, 256-wide MMAs, single-buffered accumulator */
 #define TANG_FUSED_PAIR 0x1000    /* the same kernel on CTA pairs (cta_group::2): every MMA covers two
                                      SMs' tiles (M = 256) and each SM streams half of each weight tile */
+#define TANG_FUSED_SPLIT 0x3000   /* fused paths only: the same network (the N=256 kernel without its
+                                     search warps) writes each packet's predicted tuple into `ids`,
+                                     then the search kernel, with the whole GPU, reads it there and
+                                     overwrites it with the rule id. No scratch memory. Faster than the
+                                     one persistent kernel (128 search threads per SM) when the ruleset
+                                     holds long runs under one key; the autotuner measures both. */
 #define TANG_VARIANT_MASK 0x3000
 /* Post-verification exactly as §5.1.1 prints it, for measurement only: a match in the predicted
  * tuple is returned at once, without the conflict-set probes, so a packet can get a
@@ -199,7 +205,7 @@ int tang_load_model(tang_ctx *ctx, uint32_t rs, const void *blob, size_t bytes);
  * with every path; the default (flag clear) is the exact search. */
 #define TANG_SEARCH_PAPER 0x4000
 /* Scan every rule run with one thread, as the first builds did, instead of letting the lanes of a
- * warp scan a long run (more than 16 rules under one key) together with coalesced reads; for
+ * warp scan a long run (past its first 32 rules under one key) together with coalesced reads; for
  * measurement. Ids and counters are the same either way. Combines with every path. */
 #define TANG_SEARCH_SERIAL 0x8000
 
@@ -464,14 +470,15 @@ int tang_debug_set_pool_view(tang_ctx *ctx, uint32_t rs, uint32_t n);
  * ------------------------------------------------------------------------------------- */
 
 /* Time the launch variants of a path on `n` device headers and keep the fastest per
- * (ruleset, path): for the fused paths the tensor-core kernel variant (one CTA per SM or CTA
- * pairs) and its persistent CTA count, for the search-kernel paths the block size and blocks
- * per SM. Drops captured graphs
+ * (ruleset, path): for the fused paths the tensor-core kernel variant (one CTA per SM, CTA
+ * pairs, or network and search as two kernels) and its persistent CTA count, for the
+ * search-kernel paths the block size and blocks per SM. Drops captured graphs
  * (they hold the previous launch shape). Synchronous. */
 int tang_autotune(tang_ctx *ctx, uint32_t rs, const tang_header *d_headers, uint32_t n, uint32_t flags);
 
 /* The launch shape tang_autotune chose for (rs, path): variant = the fused kernel variant
- * (0 = library default, 5 = the N=256 kernel on one SM, 6 = the same on CTA pairs),
+ * (0 = library default, 5 = the N=256 kernel on one SM, 6 = the same on CTA pairs, 7 = the
+ * network and the search as two kernels, TANG_FUSED_SPLIT; fused paths only),
  * grid = persistent CTAs (0 = one per SM), search_threads / search_bps = the search kernel's
  * block size and blocks per SM (0 = default), ms = the time per call measured for the choice
  * (0 if the path was never tuned). Outputs may be NULL. */
@@ -480,7 +487,7 @@ int tang_autotune_get(tang_ctx *ctx, uint32_t rs, uint32_t path, int *variant, i
 
 /* Set the launch shape of (rs, path) as tang_autotune would, e.g. one saved from
  * tang_autotune_get in an earlier process, so that a restart needs no new tuning. Values as in
- * tang_autotune_get (0 = default for each): variant 0, 5 or 6, grid 0 to the SM count,
+ * tang_autotune_get (0 = default for each): variant 0, 5 or 6 (7 on fused paths), grid 0 to the SM count,
  * search_threads 0 / 128 / 256 / 512, search_bps 0-16 with threads x blocks <= 2048. Drops
  * captured graphs. Errors: TANG_ENOTFOUND, TANG_EINVAL (a value out of range). */
 int tang_autotune_set(tang_ctx *ctx, uint32_t rs, uint32_t path, int variant, int grid, int search_threads,

@@ -27,8 +27,8 @@ PATHS = {
     "staged_bf16": PATH_STAGED_BF16, "no_nn": PATH_NO_NN, "staged_fp8": PATH_STAGED_FP8,
 }
 MEM_DEVICE, MEM_HOST, GRAPH = 0x00, 0x10, 0x100
-FUSED_N256, FUSED_PAIR = 0x2000, 0x1000
-VARIANTS = {None: 0, "n256": FUSED_N256, "pair": FUSED_PAIR}
+FUSED_N256, FUSED_PAIR, FUSED_SPLIT = 0x2000, 0x1000, 0x3000
+VARIANTS = {None: 0, "n256": FUSED_N256, "pair": FUSED_PAIR, "split": FUSED_SPLIT}
 SEARCH_PAPER = 0x4000
 SEARCH_SERIAL = 0x8000
 DU_NONE, DU_INCREMENTAL, DU_RETRAIN = 0, 1, 2
@@ -332,7 +332,8 @@ class Context:
     def classify(self, rs: int, headers, ids, path="fused_bf16", graph=False, stream=None, stats=False, variant=None,
                  paper=False, serial=False):
         """ids[i] = matching rule id. numpy headers/ids -> host mode; torch CUDA tensors -> device mode.
-        variant: None (tuned / default), "n256" or "pair" tensor-core kernel. paper: the paper's
+        variant: None (tuned / default), "n256" or "pair" tensor-core kernel, or "split" (fused paths:
+        the network kernel, then the search kernel in place in ids). paper: the paper's
         non-exact post-verification (TANG_SEARCH_PAPER), for measurement. serial: one thread per
         rule run (TANG_SEARCH_SERIAL), for measurement."""
         host = isinstance(headers, np.ndarray)
@@ -504,13 +505,13 @@ class Context:
         ms = ctypes.c_float()
         self._ck(lib.tang_autotune_get(self._h, rs, PATHS[path] if isinstance(path, str) else int(path),
                                        *[ctypes.byref(x) for x in v], ctypes.byref(ms)), "autotune_get")
-        names = {0: "default", 5: "n256", 6: "pair"}
+        names = {0: "default", 5: "n256", 6: "pair", 7: "split"}
         return {"variant": names.get(v[0].value, str(v[0].value)), "grid": v[1].value, "search_threads": v[2].value,
                 "search_bps": v[3].value, "ms": round(ms.value, 4)}
 
     def autotune_set(self, rs: int, path="fused_bf16", variant="default", grid=0, search_threads=0, search_bps=0):
         """Set (rs, path)'s launch shape, e.g. a dict saved from autotune_get (tang_autotune_set)."""
-        names = {"default": 0, "n256": 5, "pair": 6}
+        names = {"default": 0, "n256": 5, "pair": 6, "split": 7}
         v = names[variant] if isinstance(variant, str) else int(variant)
         self._ck(lib.tang_autotune_set(self._h, rs, PATHS[path] if isinstance(path, str) else int(path), v, int(grid),
                                        int(search_threads), int(search_bps)), "autotune_set")

@@ -117,14 +117,15 @@ int tang::check_device_error(tang_ctx *ctx) {
     return TANG_OK;
 }
 
-// Search mode bits (search_dev.cuh) requested by TANG_SEARCH_* flags.
+// Search mode bits requested by TANG_SEARCH_* flags.
 int tang::search_mode_of(uint32_t flags) {
-    return ((flags & TANG_SEARCH_PAPER) ? 1 : 0) | ((flags & TANG_SEARCH_SERIAL) ? 2 : 0);
+    return ((flags & TANG_SEARCH_PAPER) ? kSearchPaper : 0) | ((flags & TANG_SEARCH_SERIAL) ? kSearchSerial : 0);
 }
 
 // Kernel variant requested by flag bits: 5 = the N=256 fused kernel on one SM, 6 = on CTA pairs,
-// 0 = tuned or library default.
+// 7 = network and search as two kernels (fused paths), 0 = tuned or library default.
 static int variant_of(uint32_t flags) {
+    if ((flags & TANG_VARIANT_MASK) == TANG_FUSED_SPLIT) return kVariantSplit;
     if (flags & TANG_FUSED_PAIR) return 6;
     if (flags & TANG_FUSED_N256) return 5;
     return 0;
@@ -571,6 +572,17 @@ static int enqueue_classify(tang_ctx *ctx, Ruleset &rs, const tang_header *h, ui
             const int prec = path == TANG_PATH_FUSED_BF16 ? TANG_BF16 : TANG_FP8;
             if (prec == TANG_FP8 && !rs.model->has_fp8)
                 return set_err(ctx, TANG_EINVAL, "FP8 path needs a calibrated model (act_amax)");
+            if ((variant ? variant : tune ? tune->fused_variant : 0) == kVariantSplit) {
+                // the network kernel leaves each packet's predicted tuple in ids; the search kernel
+                // reads it there and overwrites it with the rule id (no scratch memory)
+                int rc = tc_launch(ctx, rs, h, n, nullptr, nullptr, reinterpret_cast<int32_t *>(ids), prec, false,
+                                   nullptr, st, nullptr, 0);
+                if (rc) return rc;
+                cudaError_t e = launch_search(rs.d_desc, uint32_t(rs.host.tuples.size()), cw, h, nullptr, n, ids,
+                                              stats, nullptr, st, smode | kSearchPredInIds);
+                if (e != cudaSuccess) return set_err(ctx, TANG_EDEVICE, "search: %s", cudaGetErrorString(e));
+                return TANG_OK;
+            }
             return tc_launch(ctx, rs, h, n, ids, nullptr, nullptr, prec, true, stats, st, tune, variant, smode);
         }
         default:

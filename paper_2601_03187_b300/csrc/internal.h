@@ -171,9 +171,18 @@ struct TuneEntry {
     int search_threads = 0;  // threads per block of the search kernel (128 / 256 / 512)
     int search_bps = 0;      // resident blocks per SM the search grid is sized for
     int fused_grid = 0;      // persistent CTAs of the fused kernel (0 = one per SM)
-    int fused_variant = 0;   // 0 = library default, 5 = the N=256 fused kernel
+    int fused_variant = 0;   // 0 = library default, 5 = the N=256 fused kernel, 6 = on CTA pairs, 7 = split
     float ms = 0.f;          // best time measured by the tuner
 };
+// Fused paths run as two kernels: the network writes its predictions into the output ids, the
+// search kernel replaces them with rule ids (TANG_FUSED_SPLIT).
+constexpr int kVariantSplit = 7;
+
+// Search mode bits: kSearchPaper = the paper's post-verification (no conflict-set probes after a
+// hit in the predicted tuple), kSearchSerial = one thread per rule run, kSearchPredInIds (search
+// kernel only) = each packet's prediction is read from its own entry of the output ids, which the
+// network kernel filled, and then overwritten with the rule id.
+constexpr int kSearchPaper = 1, kSearchSerial = 2, kSearchPredInIds = 4;
 
 struct Ruleset {
     uint32_t handle = 0;

@@ -37,9 +37,11 @@ __global__ void __launch_bounds__(THREADS) k_search(const Tables *__restrict__ d
     const uint32_t stride = gridDim.x * blockDim.x;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         const Hdr h = load_header(hdr + i);
-        const int p = pred ? __ldg(pred + i) : -1;
+        // the prediction: from its own array, from this packet's entry of ids (read before the
+        // same thread overwrites it), or none
+        const int p = pred ? __ldg(pred + i) : (mode & kSearchPredInIds) ? int(ids[i]) : -1;
         Best best;
-        const bool hit = search_packet(tb, tuples, order, h, p, best, c, mode);
+        const bool hit = search_packet(tb, tuples, order, h, p, best, c, mode & (kSearchPaper | kSearchSerial));
         ids[i] = best.id;
         if (STATS) {
             st_pk++;

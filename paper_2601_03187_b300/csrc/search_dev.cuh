@@ -170,8 +170,7 @@ __device__ __forceinline__ bool probe_tuple(const Tables &tb, const TupleDesc &d
 // a match in the predicted tuple is returned without the conflict-set probes (so it may be a
 // lower-priority rule, the uncorrected case of §5.1.1 and §8); a miss still searches the remaining
 // tuples in order. Bit kSearchSerial: every run is scanned by its own thread (no cooperative scan
-// of long runs), for measurement; the result is the same.
-constexpr int kSearchPaper = 1, kSearchSerial = 2;
+// of long runs), for measurement; the result is the same. (The bits are defined in internal.h.)
 __device__ __forceinline__ bool search_packet(const Tables &tb, const TupleDesc *tuples, const uint16_t *order,
                                               const Hdr &h, int pred, Best &best, Counters &c, int mode = 0) {
     const uint32_t T = tb.T;

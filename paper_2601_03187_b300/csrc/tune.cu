@@ -2,7 +2,9 @@
 // device batch and keeps the fastest per (ruleset, path). Candidates:
 //   search kernel (no-network, staged and plain paths): threads per block x blocks per SM;
 //   fused kernel: one CTA per SM or CTA pairs, and the number of persistent CTAs (one per SM, or a
-//   divisor-friendly subset so that the tile count spreads evenly).
+//   divisor-friendly subset so that the tile count spreads evenly); also the split form, the
+//   network kernel and then the search kernel with the whole GPU (it wins when the ruleset holds
+//   long runs, which the fused kernel's 128 search threads per SM scan slowly).
 #include <algorithm>
 
 #include "internal.h"
@@ -43,6 +45,9 @@ extern "C" int tang_autotune(tang_ctx *ctx, uint32_t rsh, const tang_header *d_h
                 e.fused_grid = g;
                 cands.push_back(e);
             }
+        TuneEntry split;
+        split.fused_variant = kVariantSplit;
+        cands.push_back(split);
     } else {
         for (int th : {128, 256, 512})
             for (int bps : {2, 4, 8, 16}) {
@@ -98,8 +103,11 @@ extern "C" int tang_autotune_set(tang_ctx *ctx, uint32_t rsh, uint32_t path, int
     if (!ctx) return TANG_EINVAL;
     auto it = ctx->rulesets.find(rsh);
     if (it == ctx->rulesets.end()) return set_err(ctx, TANG_ENOTFOUND, "unknown ruleset %u", rsh);
-    if ((variant != 0 && variant != 5 && variant != 6) || grid < 0 || grid > ctx->sm_count)
-        return set_err(ctx, TANG_EINVAL, "variant %d / grid %d out of range", variant, grid);
+    const uint32_t p = path & TANG_PATH_MASK;
+    const bool fused = p == TANG_PATH_FUSED_BF16 || p == TANG_PATH_FUSED_FP8;
+    const bool v_ok = variant == 0 || variant == 5 || variant == 6 || (variant == kVariantSplit && fused);
+    if (!v_ok || grid < 0 || grid > ctx->sm_count)
+        return set_err(ctx, TANG_EINVAL, "variant %d / grid %d out of range for path %u", variant, grid, p);
     const bool th_ok = search_threads == 0 || search_threads == 128 || search_threads == 256 || search_threads == 512;
     if (!th_ok || search_bps < 0 || search_bps > 16 || search_threads * search_bps > 2048)
         return set_err(ctx, TANG_EINVAL, "search launch %d threads x %d blocks per SM out of range", search_threads,

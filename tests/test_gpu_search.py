@@ -289,6 +289,18 @@ def test_long_runs_scanned_by_the_warp(ctx):
             assert (ids_host(ids) == want).all(), (path, serial)
             reads[(path, serial)] = (st["probes"], st["rule_reads"])
         assert reads[(path, False)] == reads[(path, True)], path
+    # the fused path as two kernels (the search with the whole GPU), and whatever the autotuner
+    # picks between the forms on this batch
+    ids = ids_dev(len(h))
+    st = ctx.classify(rs, d, ids, path="fused_bf16", stats=True, variant="split")
+    assert (ids_host(ids) == want).all()
+    assert (st["probes"], st["rule_reads"]) == reads[("fused_bf16", False)]
+    ctx.autotune(rs, d, path="fused_bf16")
+    print("autotune on long runs:", ctx.autotune_get(rs, "fused_bf16"))
+    ids = ids_dev(len(h))
+    ctx.classify(rs, d, ids, path="fused_bf16", graph=True)
+    torch.cuda.synchronize()
+    assert (ids_host(ids) == want).all()
     # predictions chosen at random: the same ids, and the oracle's probe count
     o = tss.TwoStageSearch(rules, tuples, tor)
     sub = np.arange(0, len(h), 20)

@@ -65,10 +65,17 @@ def test_config3_rulesets_every_request():
             assert (got == want).all(), sizes[k]
 
 
-def test_requests_same_alone_and_in_the_mix():
+@pytest.mark.parametrize("form", ["tuned", "split"])
+def test_requests_same_alone_and_in_the_mix(form):
+    """Each request's ids are the same alone and in the mix, and the oracle's. "split": every
+    ruleset's fused path set to the two-kernel form, whose search reads the predictions from each
+    request's own id buffer, so concurrent slots share no scratch."""
     rng = np.random.default_rng(0)
     with tg.Context(0) as ctx:
         sets = load_rulesets(ctx, [1000, 4000, 16000, 65536])
+        if form == "split":
+            for rs, _ in sets:
+                ctx.autotune_set(rs, "fused_bf16", variant="split")
         reqs = []
         for k in range(60):
             which = int(rng.integers(0, len(sets)))
@@ -194,7 +201,7 @@ def test_autotune_keeps_ids_exact():
             choice = ctx.autotune_get(rs, path)
             assert choice["ms"] > 0
             if path == "fused_bf16":
-                assert choice["variant"] in ("n256", "pair")
+                assert choice["variant"] in ("n256", "pair", "split")
             else:
                 assert choice["search_threads"] in (128, 256, 512) and choice["search_bps"] in (2, 4, 8, 16)
             ids = ids_dev(len(h))
@@ -230,6 +237,12 @@ def test_tuned_shapes_restore_in_a_new_context():
             ctx.classify(rs, d, ids, path=path, graph=True)
             torch.cuda.synchronize()
             assert (ids_host(ids) == want).all(), path
-        for bad in ({"variant": 7}, {"variant": 1}, {"grid": 100000}, {"search_threads": 96}, {"search_threads": 512, "search_bps": 8}):
+        for bad in ({"variant": 7}, {"variant": 8}, {"variant": 1}, {"grid": 100000}, {"search_threads": 96},
+                    {"search_threads": 512, "search_bps": 8}):
             with pytest.raises(tg.TangError):
                 ctx.autotune_set(rs, "no_nn", **bad)
+        # the split form exists for the fused paths only
+        ctx.autotune_set(rs, "fused_fp8", variant="split")
+        assert ctx.autotune_get(rs, "fused_fp8")["variant"] == "split"
+        with pytest.raises(tg.TangError):
+            ctx.autotune_set(rs, "staged_bf16", variant="split")

@@ -172,7 +172,26 @@ def test_ids_exact(setup, path, variant):
     assert st["pred_hit"] + st["fallback"] == len(h)
 
 
-@pytest.mark.parametrize("variant", VARIANTS)
+@pytest.mark.parametrize("path", ["fused_bf16", "fused_fp8"])
+def test_split_form_matches_the_one_kernel_form(setup, path):
+    """The fused path as two kernels (TANG_FUSED_SPLIT): the network kernel leaves each packet's
+    predicted tuple in its id, the search kernel replaces it with the rule id. Ids equal the
+    oracle's, and every counter equals the one-kernel form's: the same predictions reach the same
+    search. Also refused where it does not apply."""
+    ctx, rules, rs, T, p, amax, h = setup
+    want = oc.classify(rules, h)
+    d = to_dev(h)
+    st = {}
+    for v in ("n256", "split"):
+        ids = ids_dev(len(h))
+        st[v] = ctx.classify(rs, d, ids, path=path, stats=True, variant=v)
+        assert (ids_host(ids) == want).all(), v
+    assert st["split"] == st["n256"]
+    with pytest.raises(tg.TangError):
+        ctx.classify(rs, d, ids_dev(len(h)), path="staged_bf16", variant="split")
+
+
+@pytest.mark.parametrize("variant", VARIANTS + ["split"])
 def test_ragged_sizes_and_graph(setup, variant):
     ctx, rules, rs, T, p, amax, h = setup
     for n in (1, 5, 127, 128, 129, 255, 256, 257, 1000, 148 * 128 + 3, 74 * 256 + 129):
