@@ -453,8 +453,9 @@ def measure_model_sizes(tg, ctx, n_rules=65536, train_s=6.0, n_eval=1 << 22, sha
     the same training time for every shape, then per shape: held-out accuracy, the network's
     tuple accuracy and the paper-mode classification accuracy (the "Classi. Accu." of Tables 2-3)
     on a separate trace, the exact search's probes per packet, and the exact classification
-    throughput on the tensor-core kernel (widths 256 and 512, any depth) or, for narrower networks,
-    which only the FP32 path serves, on that path."""
+    throughput on the tensor-core kernel (widths 256 and 512, any depth; in the form the autotuner
+    picks, one kernel or split) or, for narrower networks, which only the FP32 path serves, on
+    that path."""
     import torch
     rules = wl.gen_clustered_rules(n_rules, 70)
     rs = ctx.load_ruleset(rules)
@@ -470,6 +471,10 @@ def measure_model_sizes(tg, ctx, n_rules=65536, train_s=6.0, n_eval=1 << 22, sha
                               holdout=0.05, time_budget_s=train_s, seed=73)
         ctx.load_model(rs, blob)
         path = "fused_bf16" if width in (256, 512) else "plain_fp32"
+        variant = None
+        if path == "fused_bf16":  # one kernel or the split form, whichever the autotuner measures faster
+            ctx.autotune(rs, d, path=path)
+            variant = ctx.autotune_get(rs, path)["variant"]
         st = ctx.classify(rs, d, ids, path=path, stats=True)
         ctx.classify(rs, d, ids, path=path, paper=True)
         paper_acc = float((ids == exact).float().mean().item())
@@ -485,7 +490,8 @@ def measure_model_sizes(tg, ctx, n_rules=65536, train_s=6.0, n_eval=1 << 22, sha
         e1.synchronize()
         mpkts = reps * len(ev) / (e0.elapsed_time(e1) / 1e3) / 1e6
         flops = 2 * 7 * width + blocks * 2 * 2 * width * width + 2 * width * ctx.ruleset_info(rs)["n_tuples"]
-        rows.append({"width": width, "blocks": blocks, "path": path, "mflop_per_pkt": round(flops / 1e6, 3),
+        rows.append({"width": width, "blocks": blocks, "path": path, "variant": variant,
+                     "mflop_per_pkt": round(flops / 1e6, 3),
                      "epochs": rep["epochs_run"], "holdout_accuracy": round(rep["holdout_accuracy"], 4),
                      "nn_accuracy": round(st["nn_correct"] / max(1, st["matched"]), 4),
                      "paper_classification_accuracy": round(paper_acc, 5),
