@@ -1,8 +1,9 @@
 // Fused classification kernel with 256-wide MMAs (the default tensor-core variant).
 //
-// Each tcgen05.mma here is M=128 x N=256 (K=16 BF16 / K=32 E4M3), twice the work per
-// instruction of the N=128 kernel in mlp_tc.cu; issuing the same MMA count at N=128 leaves the
-// tensor pipe about two-thirds idle. A 256-column FP32 accumulator cannot be double-buffered
+// Each tcgen05.mma here is M=128 x N=256 (K=16 BF16 / K=32 E4M3). An N=128 MMA was measured to
+// take about as many cycles as an N=256 one, so N=128 chunks would leave the tensor pipe about
+// half idle (an earlier N=128 kernel with two accumulators ran at about half this kernel's
+// rate). A 256-column FP32 accumulator cannot be double-buffered
 // next to the block input x (256 columns of packed BF16) in the 512-column TMEM, so it is
 // single-buffered and the epilogue is built to release it quickly: 16 epilogue warps (four per
 // TMEM lane quadrant) each pull their 32 rows x 64 columns into registers with two loads and

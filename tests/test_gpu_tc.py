@@ -187,6 +187,18 @@ def test_split_form_matches_the_one_kernel_form(setup, path):
         st[v] = ctx.classify(rs, d, ids, path=path, stats=True, variant=v)
         assert (ids_host(ids) == want).all(), v
     assert st["split"] == st["n256"]
+    # host buffers (the pipelined copy-in / compute / copy-out path)
+    out = np.full(len(h), 7, dtype=np.uint32)
+    ctx.classify(rs, h, out, path=path, variant="split")
+    assert (out == want).all()
+    # the paper's post-verification: not exact, but the same predictions give the same ids
+    paper = {}
+    for v in ("n256", "split"):
+        ids = ids_dev(len(h))
+        ctx.classify(rs, d, ids, path=path, variant=v, paper=True)
+        torch.cuda.synchronize()
+        paper[v] = ids_host(ids).copy()
+    assert (paper["split"] == paper["n256"]).all()
     with pytest.raises(tg.TangError):
         ctx.classify(rs, d, ids_dev(len(h)), path="staged_bf16", variant="split")
 
