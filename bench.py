@@ -739,7 +739,7 @@ def main():
     ap.add_argument("--packets", type=int, default=N_PACKETS, help="use the first P packets of the trace")
     ap.add_argument("--path", default="fused_bf16", choices=["fused_bf16", "fused_fp8"],
                     help="the timed path of --quick runs (profiling one kernel); full runs time fused_bf16")
-    ap.add_argument("--variant", default=None, choices=[None, "n256", "pair"],
+    ap.add_argument("--variant", default=None, choices=[None, "n256", "pair", "split"],
                     help="tensor-core kernel variant (default: the library's choice)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
@@ -963,6 +963,11 @@ def main():
     if rank != 0:
         return
     clocks = clk.summary()
+    # the form the headline ran in: one persistent kernel per step, or the split form (the network
+    # kernel, then the search kernel)
+    form = args.variant or tuned.get(args.path, {}).get("variant", "n256")
+    split = form == "split"
+    prec_name = "BF16" if args.path == "fused_bf16" else "E4M3"
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": "Mpkt/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True,
@@ -970,17 +975,19 @@ def main():
         "config": {"workload": "512k rules x %s-packet trace (config-0 generator; half uniform-inside-rule, half Zipf 1.2)"
                    % ("16M" if n == N_PACKETS else str(n)),
                    "rules": N_RULES, "packets_per_step": n, "tuples": T, "network": "7-512-6x(512,512)-%d" % T,
-                   "path": "fused persistent tcgen05 %s kernel, CUDA-graph replay, launch shape from the autotuner"
-                           % ("BF16" if args.path == "fused_bf16" else "E4M3"),
+                   "path": ("%s tcgen05 network kernel, then the search kernel (split form)" % prec_name if split else
+                            "fused persistent tcgen05 %s kernel" % prec_name)
+                           + ", CUDA-graph replay, form and launch shape from the autotuner",
                    "l2": "inputs (%d MB) %s L2; no flush" % (n * 16 >> 20, "larger than" if n * 16 > 126 << 20 else "NOT larger than"), "parallelism": "replicas" if world > 1 else "single"},
         "e2e": {"value": round(e2e, 3), "unit": "Mpkt/s", "h2d_bytes_per_step": n * 16, "d2h_bytes_per_step": n * 4,
                 "ids_equal_device_path": e2e_equal},
-        "gpu_launches": args.steps,
+        "gpu_launches": args.steps * (2 if split else 1),
         "roofline": {"bound": "tensor", "achieved": round(achieved_tflops, 2), "peak": peak, "unit": "TFLOP/s",
-                     "frac": round(achieved_tflops / peak, 4), "traffic": traffic_from_profile(n) if args.path == "fused_bf16" else None,
+                     "frac": round(achieved_tflops / peak, 4), "traffic": traffic_from_profile(n) if args.path == "fused_bf16" and not split else None,
                      "peak_kind": peak_kind,
                      "sm_mhz_median_here": clocks.get("sm_mhz") if isinstance(clocks, dict) else None,
-                     "flops_per_packet": fpp},
+                     "flops_per_packet": fpp,
+                     "timed": "the whole step: network kernel + search kernel" if split else "the fused kernel (one launch per step)"},
         "cpu_baseline": cpu,
         "clocks": clocks,
         "stats": {"nn_accuracy": round(st_bf16["nn_correct"] / max(1, st_bf16["matched"]), 5),
