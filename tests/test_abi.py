@@ -55,3 +55,37 @@ def test_model_blob_round_trip():
     assert (a == amax).all()
     assert (q["W0"] == p["W0"]).all() and (q["Wc"] == p["Wc"]).all()
     assert all((x == y).all() for x, y in zip(q["W2"], p["W2"]))
+
+
+def header_constants():
+    src = open(os.path.join(ROOT, "include", "tang.h")).read()
+    out = {}
+    for name, val in re.findall(r"^#define (TANG_[A-Z0-9_]+) \(?(-?(?:0x[0-9A-Fa-f]+|[0-9]+))u?\)?", src, flags=re.M):
+        out[name] = int(val, 0)
+    return out
+
+
+def test_binding_constants_match_the_header():
+    """The binding's flag and code values are the header's (a drift would send wrong flags)."""
+    from paper_2601_03187_b300 import _native as nat
+    h = header_constants()
+    pairs = {
+        "TANG_OK": nat.OK, "TANG_EINVAL": nat.EINVAL, "TANG_ENOMEM": nat.ENOMEM, "TANG_ETABLEFULL": nat.ETABLEFULL,
+        "TANG_ENOTFOUND": nat.ENOTFOUND, "TANG_EDEVICE": nat.EDEVICE, "TANG_ETIMEOUT": nat.ETIMEOUT,
+        "TANG_EUNSUPPORTED": nat.EUNSUPPORTED, "TANG_EEXIST": nat.EEXIST, "TANG_EAGAIN": nat.EAGAIN,
+        "TANG_NO_MATCH": nat.NO_MATCH, "TANG_FP32": nat.FP32, "TANG_BF16": nat.BF16, "TANG_FP8": nat.FP8,
+        "TANG_PATH_FUSED_BF16": nat.PATHS["fused_bf16"], "TANG_PATH_FUSED_FP8": nat.PATHS["fused_fp8"],
+        "TANG_PATH_PLAIN_FP32": nat.PATHS["plain_fp32"], "TANG_PATH_STAGED_BF16": nat.PATHS["staged_bf16"],
+        "TANG_PATH_NO_NN": nat.PATHS["no_nn"], "TANG_PATH_STAGED_FP8": nat.PATHS["staged_fp8"],
+        "TANG_MEM_DEVICE": nat.MEM_DEVICE, "TANG_MEM_HOST": nat.MEM_HOST, "TANG_GRAPH": nat.GRAPH,
+        "TANG_FUSED_N256": nat.VARIANTS["n256"], "TANG_FUSED_PAIR": nat.VARIANTS["pair"],
+        "TANG_FUSED_SPLIT": nat.VARIANTS["split"], "TANG_SEARCH_PAPER": nat.SEARCH_PAPER,
+        "TANG_SEARCH_SERIAL": nat.SEARCH_SERIAL, "TANG_MODEL_MAGIC": nat.MODEL_MAGIC,
+        "TANG_DU_NONE": nat.DU_NONE, "TANG_DU_INCREMENTAL": nat.DU_INCREMENTAL, "TANG_DU_RETRAIN": nat.DU_RETRAIN,
+    }
+    wrong = {k: (h.get(k), v) for k, v in pairs.items() if h.get(k) != v}
+    assert not wrong, wrong
+    # every variant flag lies inside the variant mask, and the split form is both bits
+    for k in ("TANG_FUSED_N256", "TANG_FUSED_PAIR", "TANG_FUSED_SPLIT"):
+        assert h[k] & ~h["TANG_VARIANT_MASK"] == 0, k
+    assert h["TANG_FUSED_SPLIT"] == h["TANG_FUSED_N256"] | h["TANG_FUSED_PAIR"]
