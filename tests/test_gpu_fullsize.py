@@ -107,10 +107,12 @@ def test_1m_rules_update_stream_every_batch():
         assert batches >= 40 and updates >= 2
 
 
-def test_updates_wait_for_classifications_in_flight():
+@pytest.mark.parametrize("variant", [None, "split"])
+def test_updates_wait_for_classifications_in_flight(variant):
     """A large classification issued on a side stream, then deletes and inserts with no host
     synchronisation: the classification sees the ruleset as it was (every id equals the oracle's
-    on the pre-update rules), and one issued after the updates sees the new ruleset."""
+    on the pre-update rules), and one issued after the updates sees the new ruleset. Also for the
+    split form, whose search kernel runs after the network kernel on the same stream."""
     rules = wl.rules_for_config(2)
     trace = wl.trace_for_config(2, rules, scale=0.25)
     rng = np.random.default_rng(5)
@@ -130,7 +132,7 @@ def test_updates_wait_for_classifications_in_flight():
         torch.cuda.synchronize()
         for _ in range(2):
             with torch.cuda.stream(side):
-                ctx.classify(rs, d, ids_old, path="fused_bf16", stream=side.cuda_stream)
+                ctx.classify(rs, d, ids_old, path="fused_bf16", stream=side.cuda_stream, variant=variant)
             for v in victims:
                 ctx.delete_rule(rs, int(v))
             for r in fresh:
@@ -138,7 +140,7 @@ def test_updates_wait_for_classifications_in_flight():
             ids_new = ids_dev(len(trace))
             side.wait_stream(torch.cuda.current_stream())   # the buffer's fill comes first
             with torch.cuda.stream(side):
-                ctx.classify(rs, d, ids_new, path="fused_bf16", stream=side.cuda_stream)
+                ctx.classify(rs, d, ids_new, path="fused_bf16", stream=side.cuda_stream, variant=variant)
             torch.cuda.synchronize()
             assert (ids_host(ids_old) == before).all()
             keep = ~np.isin(rules["id"], victims)
