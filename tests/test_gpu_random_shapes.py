@@ -1,7 +1,8 @@
 """Seeded random configurations of the fused tensor-core kernel against the oracle: width 256 or
 512, 1-3 residual blocks, rulesets from tens to hundreds of tuples (one or several output
-chunks), batch sizes from one packet to several tiles per CTA, BF16 and FP8. Rule ids must equal
-the linear scan's, and the predicted tuple must be the first maximum of the logits the same
+chunks), batch sizes from one packet to several tiles per CTA, BF16 and FP8, the one-kernel and
+the split form. Rule ids must equal the linear scan's, and the predicted tuple must be the first
+maximum of the logits the same
 call returns; the logits of the first 4,096 packets must match the oracle's low-precision
 forward element by element, as in test_gpu_tc.py."""
 import numpy as np
@@ -48,10 +49,11 @@ def test_random_shapes_match_the_oracle(seed):
     want = oc.classify(rules, h)
     d = to_dev(h)
     for path, prec in (("fused_bf16", tg.BF16), ("fused_fp8", tg.FP8)):
-        ids = ids_dev(n)
-        ctx.classify(rs, d, ids, path=path)
-        torch.cuda.synchronize()
-        assert (ids_host(ids) == want).all(), (seed, path, width, blocks, T, n)
+        for variant in (None, "split"):  # the one persistent kernel, and network + search kernels
+            ids = ids_dev(n)
+            ctx.classify(rs, d, ids, path=path, variant=variant)
+            torch.cuda.synchronize()
+            assert (ids_host(ids) == want).all(), (seed, path, variant, width, blocks, T, n)
         z = torch.zeros((n, T), dtype=torch.float32, device="cuda")
         t = torch.zeros(n, dtype=torch.int32, device="cuda")
         ctx.infer(rs, d, z, t, precision=prec)
